@@ -1,0 +1,364 @@
+"""Benchmark of the self-gravitating SPH step on GB300.
+
+One "step" is one predictor-corrector step of the whole hot path (HFC, SU,
+SP, neighbour lists, DC, GFC, HFC, SU) over the large two-halo collision,
+2 x (1,048,576 gas + 1,048,576 dark) = 4,194,304 particles, FP32 forces with
+FP64 leapfrog accumulators.  Metric: particle-steps per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own
+independent replica of the workload (the step does not shard across GPUs
+here: replicas only); value = particles x steps summed over ranks / the
+slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload (target rows of every stage), extrapolated to a
+whole step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (gas per halo, dark per halo, halos, seed, dt)
+    "large": (1048576, 1048576, 2, 2, 1e-3),
+    "two_halo": (131072, 131072, 2, 1, 1e-3),
+    "single": (8192, 8192, 1, 0, 1e-3),
+}
+WORKLOAD_NAMES = {
+    "large": "large two-halo collision 2x(1048576 gas + 1048576 dark), Plummer a=G=M=1",
+    "two_halo": "two-halo collision 2x(131072 gas + 131072 dark), Plummer a=G=M=1",
+    "single": "single Plummer halo 8192 gas + 8192 dark",
+}
+# FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
+
+
+def make_ic(name, rank=0):
+    from paper_1807_08116_gb300 import ics
+    g, d, halos, seed, _ = WORKLOADS[name]
+    if halos == 1:
+        return ics.single_halo(g, d, seed=seed + rank)
+    return ics.two_halo(g, d, seed=seed + rank)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(ic, rows_grav=256, rows_gas=256, seed=0):
+    """Time the FP64 oracle on `rows_grav` gravity targets (over all N sources)
+    and `rows_gas` gas targets (density + two hydro evaluations, brute force
+    over all gas), then extrapolate to one full step (two HFC, one DC, one GFC
+    per step; the O(N) integrator is timed in full).  Returns
+    (particle-steps/s, seconds per extrapolated step, threads, description)."""
+    import oracle
+    n, ng = ic["n"], ic["n_gas"]
+    rng = np.random.default_rng(seed)
+    rg = np.sort(rng.choice(n, min(rows_grav, n), replace=False)).astype(np.int32)
+    rh = np.sort(rng.choice(ng, min(rows_gas, ng), replace=False)).astype(np.int32)
+    pm = np.empty((n, 4), np.float32)
+    pm[:, :3] = ic["r"]
+    pm[:, 3] = ic["m"]
+    ph = np.empty((ng, 4), np.float32)
+    ph[:, :3] = ic["r"][:ng]
+    ph[:, 3] = ic["h"]
+    ve = np.empty((ng, 4), np.float32)
+    ve[:, :3] = ic["v"][:ng]
+    ve[:, 3] = ic["e"]
+    mass = ic["m"][:ng].astype(np.float32)
+    oracle.density(ph[:8], mass[:8])   # load / build outside the timing
+    t0 = time.perf_counter()
+    oracle.gravity(pm, rows=rg)
+    t_grav = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rho, _ = oracle.density(ph, mass, rows=rh)
+    t_dc = time.perf_counter() - t0
+    rho_all = np.ones(ng, np.float32)
+    rho_all[rh] = rho
+    t0 = time.perf_counter()
+    oracle.hydro(ph, ve, mass, rho_all, rows=rh)
+    t_hfc = time.perf_counter() - t0
+    # integrator on the whole state (both phases)
+    r = np.ascontiguousarray(ic["r"].T)
+    v = np.ascontiguousarray(ic["v"].T)
+    e = ic["e"].copy()
+    vs, es = np.zeros_like(v), np.zeros_like(e)
+    zeros_h = np.zeros((ng, 3))
+    zeros_g = np.zeros((n, 3))
+    t0 = time.perf_counter()
+    oracle.predict(ng, 1e-3, r, v, e, vs, es, zeros_h, np.zeros(ng), zeros_g)
+    oracle.correct(ng, 1e-3, v, e, vs, es, zeros_h, np.zeros(ng), zeros_g)
+    t_su = time.perf_counter() - t0
+    t_step = t_grav * n / len(rg) + (t_dc + 2 * t_hfc) * ng / len(rh) + t_su
+    threads = oracle.threads()
+    desc = (f"{len(rg)} of {n} gravity targets, {len(rh)} of {ng} gas targets (density + 2 hydro), "
+            f"brute force FP64, extrapolated to one step; integrator over all particles; "
+            f"sampled {t_grav + t_dc + t_hfc + t_su:.1f} s")
+    return n / t_step, t_step, threads, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ic = make_ic(args.workload)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, t_step, threads, desc = oracle_sample(ic, args.ref_rows, args.ref_rows, seed=k)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": "particle-steps/s", "value": value,
+        "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * ic["n"] / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "n": ic["n"], "n_gas": ic["n_gas"]},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.sim import Simulation
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    nv.lib()
+    ic = make_ic(args.workload, rank)
+    n, ng = ic["n"], ic["n_gas"]
+    dt = WORKLOADS[args.workload][4]
+    sim = Simulation(ic)
+    sim.initial_rhs()
+    for _ in range(args.warmup):
+        sim.step(dt)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ------------------------------------
+    evs = [nv.StageEvents() for _ in range(args.steps)]
+    stream = torch.cuda.current_stream()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = nv.sph_launch_count()
+    t_start.record(stream)
+    for k in range(args.steps):
+        sim.state.events = evs[k].ptr
+        sim.step(dt, check=False)
+    t_stop.record(stream)
+    launches = nv.sph_launch_count() - launches0
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    sim.state.events = None
+    flags = sim.ctx.device_status() if sim.ctx is not None else 0
+    if flags:
+        raise RuntimeError(f"device status flags {flags} during the timed steps")
+    ms = t_start.elapsed_time(t_stop)
+    stage = {name: float(np.mean([e.stage_ms()[name] for e in evs])) for name in nv.STAGES}
+    for e in evs:
+        e.close()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(sim, args, dt, barrier, dist, world, n, ng)
+
+    # ---- roofline of the dominant kernel (gravity) -------------------------
+    gfc_ms = stage["gfc"]
+    achieved = FLOP_PER_INTERACTION * float(n) * float(n) / (gfc_ms / 1e3) / 1e12
+    R, S = nv.sph_gravity_plan(n)
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": args.gfc_traffic,
+            "kernel": "pp_gravity_kernel", "interactions_per_s": float(n) * n / (gfc_ms / 1e3),
+            "flop_per_interaction": FLOP_PER_INTERACTION,
+            "peak_note": "FP32 pipe 152 SM x 128 lanes x 2 flop x 2.07 GHz (derived, not measured)",
+            "plan": {"targets_per_thread": R, "cluster_split": S}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, t_step, threads, desc = oracle_sample(ic, args.cpu_rows, args.cpu_rows)
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES[args.workload], "n": n, "n_gas": ng, "dt": dt,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state and lists > 129 MB)",
+                       "precision": "FP32 forces (Kahan), FP64 leapfrog state"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "stage_ms": stage,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(sim, args, dt, barrier, dist, world, n, ng):
+    """Same metric through the C-ABI step with the state in pinned host
+    memory: every step uploads r, v, e, h, runs sph_step and downloads r, v, e."""
+    import torch
+
+    from paper_1807_08116_gb300 import native as nv
+    t = sim.t
+    host = {k: torch.empty(t[k].shape, dtype=t[k].dtype, pin_memory=True)
+            for k in ("r", "v", "e", "h")}
+    for k in host:
+        host[k].copy_(t[k])
+    torch.cuda.synchronize()
+    h2d = sum(host[k].numel() * host[k].element_size() for k in ("r", "v", "e", "h"))
+    d2h = sum(host[k].numel() * host[k].element_size() for k in ("r", "v", "e"))
+    steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for k in ("r", "v", "e", "h"):
+            t[k].copy_(host[k], non_blocking=True)
+        nv.sph_step(sim.ctx, sim.state, dt)
+        for k in ("r", "v", "e"):
+            host[k].copy_(t[k], non_blocking=True)
+        torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    if dist is not None:
+        x = torch.tensor([el], device="cuda")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        el = float(x.item())
+    return {"value": world * n * steps / el, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=512,
+                    help="target rows per stage of each reference-arm step sample")
+    ap.add_argument("--cpu-rows", type=int, default=2048,
+                    help="target rows per stage of the cpu_baseline sample")
+    ap.add_argument("--gfc-traffic", type=float, default=None,
+                    help="DRAM bytes per gravity launch from an ncu capture of this workload")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,299 @@
+/*
+ * sphgb.h -- C ABI of the GB300 (sm_103a) self-gravitating SPH right-hand
+ * side of Khrapov & Khoperskov, "Smoothed-Particle Hydrodynamics Models:
+ * Implementation Features on GPUs" (arXiv:1807.08116).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* or documented as "device" are CUDA device pointers
+ *    owned by the caller; the library never frees or reallocates them and
+ *    never calls cudaMalloc.  Host pointers are named h_* or documented.
+ *  - Particle arrays are in the caller's ("original") order, gas particles
+ *    first: indices [0, n_gas) are gas (SPH), [n_gas, n) are collisionless.
+ *  - float4 arrays are passed as float* with 4 floats per particle (16-byte
+ *    aligned); FP64 vectors are structure-of-arrays: r[3*n] holds x[0..n),
+ *    y[0..n), z[0..n).
+ *  - Every call that takes a stream is asynchronous with respect to the host
+ *    unless stated otherwise and returns an int status (SPH_OK or an error
+ *    code below).  Argument errors are detected on the host before anything
+ *    is launched.  Errors found by a kernel (a too-wide search, an exhausted
+ *    list capacity, a wait that ran out of time) are recorded in a device
+ *    status word and read with sph_ctx_device_status / pp_gravity_status.
+ *  - Counts are int32: n < 2^31, and the total neighbour-list length < 2^31.
+ *  - No C++ exception crosses this boundary.
+ */
+#ifndef SPHGB_H
+#define SPHGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *sph_stream_t;
+
+/* Status codes. */
+#define SPH_OK               0
+#define SPH_ERR_INVALID_ARG  1  /* a pointer, size or parameter is out of range */
+#define SPH_ERR_CUDA         2  /* a CUDA runtime call failed */
+#define SPH_ERR_NB_OVERFLOW  3  /* neighbour lists exceed the context capacity */
+#define SPH_ERR_BUDGET       4  /* serving: request exceeds the memory budget */
+#define SPH_ERR_TIMEOUT      5  /* a bounded device wait ran out */
+#define SPH_ERR_NOT_FOUND    6  /* serving: unknown job id */
+#define SPH_ERR_DEVICE       7  /* a kernel recorded an error in the status word */
+
+/* Device status-word bits (sph_ctx_device_status, pp_gravity_status). */
+#define SPH_FLAG_NB_OVERFLOW   1   /* neighbour entries beyond capacity were dropped */
+#define SPH_FLAG_SEARCH_WIDE   2   /* a search box exceeded 2^24 cells and was skipped */
+#define SPH_FLAG_TIMEOUT       4   /* a bounded mbarrier wait gave up */
+#define SPH_FLAG_ROW_UNSORTED  8   /* a segment too long to canonicalise was left as is */
+
+/* Model constants (Sect. 2): gravitational constant G and softening length
+ * eps of Eq. 4 (Plummer form, |dr|^2 + eps^2); adiabatic index gamma of
+ * Eq. 5; artificial-viscosity alpha, beta, eta (after Eq. 11); smoothing-
+ * length factor sigma of h = sigma (m / rho)^(1/3) (after Eq. 8). */
+typedef struct SphParams {
+    float G, eps, gamma, alpha, beta, eta, sigma;
+} SphParams;
+
+/* Multi-level hashed grid of the sorting stage (Sect. 3, "hierarchical grid
+ * sorting").  A gas particle with smoothing length h is on level l, the
+ * smallest l >= 0 with h <= L0 * 2^l (L0 = 2^log2_L0), clamped to
+ * n_levels - 1.  Its cell on that level is floor((x - x0) / (L0 * 2^l)) per
+ * axis in FP32, clamped to [0, 2^21 - 1]; its bucket (the paper's cell index
+ * k of CellSPH) is (bit-interleave(cx, cy, cz) + l * 0x9E3779B97F4A7C15)
+ * mod 2^log2_M. */
+typedef struct SphGrid {
+    float x0, y0, z0;
+    int32_t log2_L0;   /* in [-100, 100] */
+    int32_t n_levels;  /* in [1, 32] */
+    int32_t log2_M;    /* in [4, 30]; must equal the context's */
+} SphGrid;
+
+/* ------------------------------------------------------------------------ */
+/* Context: the scratch of the sorting, neighbour and SPH stages.           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sph_ctx sph_ctx;
+
+/* Bytes of device workspace a context for up to n_gas_max gas particles,
+ * 2^log2_M buckets and nb_capacity neighbour entries needs.  Returns 0 on
+ * invalid arguments. */
+size_t sph_ctx_workspace_bytes(int32_t n_gas_max, int32_t log2_M, int64_t nb_capacity);
+
+/* Create a context over caller-allocated device workspace d_workspace of
+ * workspace_bytes (>= sph_ctx_workspace_bytes(...), 256-byte aligned).  The
+ * context carves all its arrays out of that buffer; the caller keeps
+ * ownership and must keep it alive until sph_ctx_destroy.  Zero-fills the
+ * workspace on `stream`.  *out receives a host-side handle. */
+int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_t log2_M,
+                   int64_t nb_capacity, void *d_workspace, size_t workspace_bytes,
+                   sph_stream_t stream, sph_ctx **out);
+
+/* Release the host-side handle (not the workspace). */
+int sph_ctx_destroy(sph_ctx *ctx);
+
+/* Replace the model constants used by later calls. */
+int sph_ctx_set_params(sph_ctx *ctx, const SphParams *params);
+
+/* Synchronise `stream`, then read and clear the context's device status word
+ * (SPH_FLAG_* bits) into *h_flags.  Returns SPH_ERR_DEVICE if any bit was
+ * set, SPH_OK otherwise. */
+int sph_ctx_device_status(sph_ctx *ctx, sph_stream_t stream, int32_t *h_flags);
+
+/* Synchronise `stream` and read the grid the last sph_bin_and_sort used. */
+int sph_ctx_get_grid(sph_ctx *ctx, sph_stream_t stream, SphGrid *h_grid);
+
+/* Synchronise `stream` and read the total neighbour-list length of the last
+ * sph_build_neighbors (its "needed" capacity). */
+int sph_ctx_nb_total(sph_ctx *ctx, sph_stream_t stream, int64_t *h_total);
+
+/* ------------------------------------------------------------------------ */
+/* Stage SP: grid sorting of the gas particles (Sect. 3, SP0..SP4).          */
+/* ------------------------------------------------------------------------ */
+
+/* Bin the n_gas gas particles d_pos_h ([n_gas][4]: x, y, z, h) into buckets
+ * and counting-sort them: bucket counts with atomics (SP1), an exclusive
+ * prefix sum over the 2^log2_M buckets with a warp-shuffle / shared-memory
+ * cascade (SP2, SP3), and a scatter into bucket order (SP4), canonicalised so
+ * that particles inside one bucket are in ascending original index (a stable
+ * counting sort).  h_grid != NULL fixes the grid; h_grid == NULL derives it
+ * on the device from the particles (x0 = floor(min x) - 1 per axis,
+ * L0 = 2^ceil(log2 min h), enough levels for max h).  The context keeps the
+ * sorted working set for the following stages.  Optional copies of the
+ * results (NULL to skip): d_key_out[n_gas] bucket of each particle,
+ * d_cell_start_out[M + 1] exclusive bucket starts (the paper's inclusive
+ * CellSPH[k].y is cell_start[k + 1]), d_perm_out[n_gas] original index of
+ * each sorted slot. */
+int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_gas,
+                     const SphGrid *h_grid, int32_t *d_key_out,
+                     int32_t *d_cell_start_out, int32_t *d_perm_out,
+                     sph_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour lists (used by DC and HFC, Sect. 3).                            */
+/* ------------------------------------------------------------------------ */
+
+/* Build the neighbour list of every gas particle of the last sort: all gas
+ * j != i with (in FP32) ((dx*dx + dy*dy) + dz*dz) < (h_i + h_j)^2, i.e.
+ * |r_ij| < 2 h_ij, the support of W and W_p (Eqs. 8-9).  Lists are CSR in
+ * sorted space: row s (sorted slot) spans [nb_start[s], nb_start[s+1]) and
+ * holds sorted slots; perm maps slots to original indices.  The order inside
+ * a row is deterministic.
+ * If h_needed != NULL the call synchronises `stream`, writes the total list
+ * length to *h_needed and returns SPH_ERR_NB_OVERFLOW (lists not built) when
+ * it exceeds the context capacity.  If h_needed == NULL the call stays
+ * asynchronous and an overflow sets SPH_FLAG_NB_OVERFLOW instead.
+ * Optional copies (NULL to skip): d_nb_start_out[n_gas + 1] and
+ * d_nb_idx_out[out_capacity] (copied only if the total fits). */
+int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_start_out,
+                        int32_t *d_nb_idx_out, int64_t out_capacity,
+                        int64_t *h_needed, sph_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Stage DC: density (Eq. 7) and the next smoothing length.                 */
+/* ------------------------------------------------------------------------ */
+
+/* rho_i = m_i W(0, h_i) + sum_{j in list(i)} m_j W(|r_ij|, h_ij), the cubic
+ * spline W of Eq. 8, h_ij = (h_i + h_j)/2; then h_next_i = sigma
+ * (m_i / rho_i)^(1/3).  d_mass[n_gas] is in original order; d_rho[n_gas] and
+ * d_h_next[n_gas] are written in original order.  FP32 with compensated
+ * summation. */
+int sph_density(sph_ctx *ctx, int32_t n_gas, const float *d_mass, float *d_rho,
+                float *d_h_next, sph_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Stage HFC: hydrodynamic accelerations and heating (Eqs. 10-11).           */
+/* ------------------------------------------------------------------------ */
+
+/* a_i = -sum_j m_j Pi_ij grad W_p(|r_ij|, h_ij) and de_i/dt = 1/2 sum_j m_j
+ * Pi_ij dv_ij . grad W_p over the neighbour list, with Pi_ij = p_i/rho_i^2
+ * + p_j/rho_j^2 + nu_ij (Monaghan viscosity, Sect. 2.2), p = (gamma - 1)
+ * rho e (Eq. 5), c = sqrt(gamma p / rho) (0 if p < 0), grad W_p = 0 at
+ * |r_ij| = 0.  Inputs in original order: d_vel_e[n_gas][4] (vx, vy, vz, e),
+ * d_rho[n_gas], d_mass[n_gas]; output d_acc_dedt[n_gas][4] (ax, ay, az,
+ * de/dt) in original order.  Positions and h are those of the last sort.
+ * FP32 with compensated (Kahan) summation. */
+int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+               const float *d_mass, float *d_acc_dedt, sph_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Stage GFC: direct particle-particle gravity (Eq. 4).                      */
+/* ------------------------------------------------------------------------ */
+
+#define SPH_GRAV_POTENTIAL 1  /* also write phi_i = -G sum_{j!=i} m_j / sqrt(r^2+eps^2) */
+#define SPH_GRAV_NO_KAHAN  2  /* plain FP32 running sums instead of per-tile compensation */
+
+/* g_i = -G sum_{j != i} m_j (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^(3/2) over
+ * all n particles (gas and dark), the Plummer-softened reading of Eq. 4.
+ * d_pos_m[n][4] = (x, y, z, m); d_acc_pot[n][4] = (gx, gy, gz, phi) with
+ * phi = 0 unless SPH_GRAV_POTENTIAL.  eps >= 0; with eps = 0 coincident
+ * pairs contribute nothing.  No context: the j-range is split across the
+ * CTAs of a thread-block cluster and reduced through distributed shared
+ * memory, so the call needs no scratch.  n = 0 is a no-op. */
+int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
+               int32_t flags, sph_stream_t stream);
+
+/* Launch plan pp_gravity uses for n particles and `flags`: *h_R targets per
+ * thread (256 R per CTA) and the cluster split *h_S of the source range. */
+int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t *h_S);
+
+/* Synchronise `stream`, read and clear the gravity kernel's device status
+ * word (SPH_FLAG_TIMEOUT).  Returns SPH_ERR_DEVICE if a bit was set. */
+int pp_gravity_status(sph_stream_t stream, int32_t *h_flags);
+
+/* ------------------------------------------------------------------------ */
+/* Stage SU: leapfrog predictor-corrector (Eqs. 12-16).                      */
+/* ------------------------------------------------------------------------ */
+
+#define SPH_PREDICT 0  /* Eqs. 12-14 */
+#define SPH_CORRECT 1  /* Eqs. 15-16 */
+#define SPH_EMIT    2  /* no update: only write the FP32 working copies */
+
+/* FP64 state (device, SoA): d_r[3n], d_v[3n], d_e[n_gas], and the saved
+ * d_v_save[3n], d_e_save[n_gas] (written by PREDICT, read by CORRECT).
+ * Accelerations Q_i = a_hyd_i + g_i for gas, g_i for dark, E_i = de_i/dt:
+ * d_acc_hyd[n_gas][4] (ax, ay, az, de/dt), d_grav[n][4].
+ * PREDICT: v_save = v, e_save = e, v <- v + dt Q, e <- e + dt E,
+ *          r <- r + dt/2 (v_new + v_save).
+ * CORRECT: v <- (v_save + v)/2 + dt/2 Q, e <- (e_save + e)/2 + dt/2 E.
+ * Then (all phases) writes the FP32 working copies, each optional (NULL to
+ * skip): d_pos_m[n][4] = (x, y, z, m), d_pos_h[n_gas][4] = (x, y, z, h),
+ * d_vel_e[n_gas][4] = (vx, vy, vz, e), from d_mass[n] and d_h[n_gas]. */
+int integrate_step(int32_t phase, double dt, int32_t n, int32_t n_gas, double *d_r,
+                   double *d_v, double *d_e, double *d_v_save, double *d_e_save,
+                   const float *d_acc_hyd, const float *d_grav, const float *d_mass,
+                   const float *d_h, float *d_pos_m, float *d_pos_h, float *d_vel_e,
+                   sph_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Whole steps.                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Device arrays of one simulation (caller-owned, original order). */
+typedef struct SphState {
+    int32_t n, n_gas;
+    double *r, *v, *e;            /* FP64 state: [3n], [3n], [n_gas] */
+    double *v_save, *e_save;      /* predictor saves: [3n], [n_gas] */
+    float *mass;                  /* [n] */
+    float *h;                     /* [n_gas] smoothing length for the next evaluation */
+    float *pos_m;                 /* [n][4] FP32 working copy (x, y, z, m) */
+    float *pos_h;                 /* [n_gas][4] FP32 working copy (x, y, z, h) */
+    float *vel_e;                 /* [n_gas][4] FP32 working copy (vx, vy, vz, e) */
+    float *rho;                   /* [n_gas] density of the current evaluation */
+    float *acc_hyd;               /* [n_gas][4] (ax, ay, az, de/dt) */
+    float *grav;                  /* [n][4] (gx, gy, gz, phi) */
+    int32_t fresh;                /* 1 after sph_rhs_initial: the next step reuses its RHS */
+    int32_t grav_flags;           /* flags passed to pp_gravity */
+    void **events;                /* NULL, or 2 * SPH_NUM_STAGES cudaEvent_t (see sph_step) */
+} SphState;
+
+/* Stages of one sph_step, in launch order. */
+#define SPH_STAGE_HFC_PRED 0  /* HFC at (r_n, v_n, e_n) */
+#define SPH_STAGE_SU_PRED  1  /* predictor, Eqs. 12-14 */
+#define SPH_STAGE_SP       2  /* grid sort */
+#define SPH_STAGE_NB       3  /* neighbour lists */
+#define SPH_STAGE_DC       4  /* density, Eq. 7 */
+#define SPH_STAGE_GFC      5  /* gravity, Eq. 4 */
+#define SPH_STAGE_HFC_CORR 6  /* HFC at (r_{n+1}, v~, e~) */
+#define SPH_STAGE_SU_CORR  7  /* corrector, Eqs. 15-16 */
+#define SPH_NUM_STAGES     8
+
+/* First right-hand-side evaluation at the current state: FP32 working
+ * copies, SP, neighbour lists, DC (rho, next h), GFC and HFC.  Sets fresh. */
+int sph_rhs_initial(sph_ctx *ctx, SphState *st, sph_stream_t stream);
+
+/* One predictor-corrector step of size dt (Sect. 2.2): HFC at (r, v, e)
+ * unless fresh; PREDICT; SP; neighbour lists; DC; GFC once per step at the
+ * new positions; HFC at (r', v~, e~); CORRECT.  SP, DC and HFC are skipped
+ * when n_gas == 0 (collisionless run).  Asynchronous: a neighbour-list
+ * overflow shows as SPH_FLAG_NB_OVERFLOW in the device status word.
+ * If st->events != NULL, events[2 s] and events[2 s + 1] are recorded on
+ * `stream` before and after stage s (SPH_STAGE_*; a skipped stage records
+ * both back to back). */
+int sph_step(sph_ctx *ctx, SphState *st, double dt, sph_stream_t stream);
+
+/* FP64 reductions of one state in a fixed order (deterministic) by one
+ * thread block: d_out[8] (device) = {kinetic sum m v^2 / 2, thermal
+ * sum_gas m e, potential sum m phi / 2 (phi read from grav.w), px, py, pz,
+ * total mass, 0}. */
+int sph_diagnostics(const SphState *st, double *d_out, sph_stream_t stream);
+
+/* Timing helpers over the CUDA runtime (for callers without their own):
+ * create / destroy `count` timing-enabled events into h_events[count], and
+ * the elapsed milliseconds between two recorded events (synchronises on b). */
+int sph_events_create(int32_t count, void **h_events);
+int sph_events_destroy(int32_t count, void **h_events);
+int sph_event_elapsed_ms(void *a, void *b, float *h_ms);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t sph_launch_count(void);
+
+int sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHGB_H */

@@ -60,6 +60,8 @@ def _load():
             P = ctypes.c_void_p
             I = ctypes.c_int
             D = ctypes.c_double
+            lib.oracle_threads.restype = I
+            lib.oracle_threads.argtypes = []
             lib.oracle_W.restype = D
             lib.oracle_W.argtypes = [D, D]
             lib.oracle_Wp.restype = D
@@ -95,6 +97,11 @@ def _rows(rows, n):
     if rows is None:
         return np.arange(n, dtype=np.int32)
     return _c(rows, np.int32)
+
+
+def threads() -> int:
+    """Number of host threads the oracle's parallel loops use."""
+    return int(_load().oracle_threads())
 
 
 # -- kernels (Eqs. 8, 9) ------------------------------------------------------

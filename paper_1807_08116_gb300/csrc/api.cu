@@ -1,0 +1,480 @@
+// api.cu -- the C ABI of include/sphgb.h: context over caller-owned
+// workspace, the stage entry points SP / neighbour lists / DC / HFC, and the
+// whole-step driver that sequences them as the paper's predictor-corrector
+// flow (Sect. 2.2 and the kernel list of Sect. 3).
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace sphgb;
+
+namespace sphgb {
+static std::atomic<long long> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace sphgb
+
+extern "C" int64_t sph_launch_count(void) { return g_launches.load(); }
+
+extern "C" int sph_events_create(int32_t count, void **h_events) {
+    if (count < 0 || (count > 0 && !h_events)) return SPH_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy((cudaEvent_t)h_events[j]);
+            return SPH_ERR_CUDA;
+        }
+        h_events[i] = (void *)e;
+    }
+    return SPH_OK;
+}
+
+extern "C" int sph_events_destroy(int32_t count, void **h_events) {
+    if (count < 0 || (count > 0 && !h_events)) return SPH_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (h_events[i]) cudaEventDestroy((cudaEvent_t)h_events[i]);
+    return SPH_OK;
+}
+
+extern "C" int sph_event_elapsed_ms(void *a, void *b, float *h_ms) {
+    if (!a || !b || !h_ms) return SPH_ERR_INVALID_ARG;
+    SPH_CUDA_TRY(cudaEventSynchronize((cudaEvent_t)b));
+    SPH_CUDA_TRY(cudaEventElapsedTime(h_ms, (cudaEvent_t)a, (cudaEvent_t)b));
+    return SPH_OK;
+}
+
+struct sph_ctx {
+    SphParams params;
+    int n_max;
+    int log2_M;
+    long long M;
+    long long capacity;
+    void *ws;
+    size_t ws_bytes;
+    // carved arrays
+    int *key, *count, *start, *perm, *tmp, *long_list, *long_count;
+    unsigned *hmax_cell;
+    int *lvl_count;
+    unsigned *lvl_hmax;
+    GridDev *grid;
+    unsigned *red;
+    int *flags;
+    int *block_sums;
+    float4 *pos_h_s, *vel_s, *aux_s;
+    float *rho_s, *mass_s;
+    int *own, *rev, *row_len, *nb_start, *nb_idx;
+    int n_sorted;    // n_gas of the last sort
+    int nb_built;    // 1 once lists match the last sort
+};
+
+namespace {
+
+struct Carver {
+    char *base;
+    size_t off;
+    template <class T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void carve(sph_ctx *c, char *base, size_t *total) {
+    Carver cv{base, 0};
+    const size_t n = (size_t)c->n_max, M = (size_t)c->M;
+    const size_t seg_list = n > M ? n : M;
+    c->key = cv.take<int>(n);
+    c->count = cv.take<int>(M);
+    c->start = cv.take<int>(M + 1);
+    c->hmax_cell = cv.take<unsigned>(M);
+    c->perm = cv.take<int>(n);
+    c->tmp = cv.take<int>(c->capacity > (long long)n ? (size_t)c->capacity : n);
+    c->long_list = cv.take<int>(seg_list);
+    c->long_count = cv.take<int>(4);
+    c->lvl_count = cv.take<int>(kMaxLevels);
+    c->lvl_hmax = cv.take<unsigned>(kMaxLevels);
+    c->grid = cv.take<GridDev>(1);
+    c->red = cv.take<unsigned>(8);
+    c->flags = cv.take<int>(4);
+    size_t nb_scan = (size_t)scan_block_count((long long)(M > n ? M : n));
+    c->block_sums = cv.take<int>(nb_scan + 32);
+    c->pos_h_s = cv.take<float4>(n);
+    c->vel_s = cv.take<float4>(n);
+    c->aux_s = cv.take<float4>(n);
+    c->rho_s = cv.take<float>(n);
+    c->mass_s = cv.take<float>(n);
+    c->own = cv.take<int>(n);
+    c->rev = cv.take<int>(n);
+    c->row_len = cv.take<int>(n);
+    c->nb_start = cv.take<int>(n + 1);
+    c->nb_idx = cv.take<int>((size_t)c->capacity);
+    *total = (cv.off + 255) & ~size_t(255);
+}
+
+bool params_ok(const SphParams *p) {
+    return p && p->G == p->G && p->eps >= 0.0f && p->gamma > 1.0f && p->alpha >= 0.0f &&
+           p->beta >= 0.0f && p->eta >= 0.0f && p->sigma > 0.0f;
+}
+
+HydroParams hydro_params(const sph_ctx *c) {
+    return HydroParams{c->params.gamma, c->params.alpha, c->params.beta, c->params.eta,
+                       c->params.sigma};
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" int sph_version(void) { return 1; }
+
+extern "C" size_t sph_ctx_workspace_bytes(int32_t n_gas_max, int32_t log2_M, int64_t nb_capacity) {
+    if (n_gas_max < 0 || log2_M < 4 || log2_M > 30 || nb_capacity < 0 ||
+        nb_capacity > 0x7fffffffLL)
+        return 0;
+    sph_ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.n_max = n_gas_max;
+    c.log2_M = log2_M;
+    c.M = 1ll << log2_M;
+    c.capacity = nb_capacity;
+    size_t total = 0;
+    carve(&c, nullptr, &total);
+    return total;
+}
+
+extern "C" int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_t log2_M,
+                              int64_t nb_capacity, void *d_workspace, size_t workspace_bytes,
+                              sph_stream_t stream, sph_ctx **out) {
+    if (!out || !params_ok(params) || !d_workspace) return SPH_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255u) != 0) return SPH_ERR_INVALID_ARG;
+    size_t need = sph_ctx_workspace_bytes(n_gas_max, log2_M, nb_capacity);
+    if (need == 0 || workspace_bytes < need) return SPH_ERR_INVALID_ARG;
+    sph_ctx *c = new (std::nothrow) sph_ctx;
+    if (!c) return SPH_ERR_INVALID_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->params = *params;
+    c->n_max = n_gas_max;
+    c->log2_M = log2_M;
+    c->M = 1ll << log2_M;
+    c->capacity = nb_capacity;
+    c->ws = d_workspace;
+    c->ws_bytes = workspace_bytes;
+    size_t total = 0;
+    carve(c, static_cast<char *>(d_workspace), &total);
+    if (cudaMemsetAsync(d_workspace, 0, total, (cudaStream_t)stream) != cudaSuccess) {
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_destroy(sph_ctx *ctx) {
+    delete ctx;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_set_params(sph_ctx *ctx, const SphParams *params) {
+    if (!ctx || !params_ok(params)) return SPH_ERR_INVALID_ARG;
+    ctx->params = *params;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_device_status(sph_ctx *ctx, sph_stream_t stream, int32_t *h_flags) {
+    if (!ctx || !h_flags) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    SPH_CUDA_TRY(cudaMemcpyAsync(&v, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->flags, 0, sizeof(int), st));
+    SPH_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_flags = v;
+    return v ? SPH_ERR_DEVICE : SPH_OK;
+}
+
+extern "C" int sph_ctx_get_grid(sph_ctx *ctx, sph_stream_t stream, SphGrid *h_grid) {
+    if (!ctx || !h_grid) return SPH_ERR_INVALID_ARG;
+    GridDev g;
+    cudaStream_t st = (cudaStream_t)stream;
+    SPH_CUDA_TRY(cudaMemcpyAsync(&g, ctx->grid, sizeof(g), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA_TRY(cudaStreamSynchronize(st));
+    h_grid->x0 = g.x0;
+    h_grid->y0 = g.y0;
+    h_grid->z0 = g.z0;
+    h_grid->log2_L0 = g.log2_L0;
+    h_grid->n_levels = g.n_levels;
+    h_grid->log2_M = g.log2_M;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_nb_total(sph_ctx *ctx, sph_stream_t stream, int64_t *h_total) {
+    if (!ctx || !h_total) return SPH_ERR_INVALID_ARG;
+    int t = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    SPH_CUDA_TRY(cudaMemcpyAsync(&t, ctx->nb_start + ctx->n_sorted, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+    SPH_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_total = t;
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SP
+// ---------------------------------------------------------------------------
+
+extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_gas,
+                                const SphGrid *h_grid, int32_t *d_key_out,
+                                int32_t *d_cell_start_out, int32_t *d_perm_out,
+                                sph_stream_t stream) {
+    if (!ctx || n_gas < 0 || n_gas > ctx->n_max) return SPH_ERR_INVALID_ARG;
+    if (n_gas > 0 && (!d_pos_h || !aligned16(d_pos_h))) return SPH_ERR_INVALID_ARG;
+    if (h_grid) {
+        if (h_grid->log2_M != ctx->log2_M || h_grid->n_levels < 1 || h_grid->n_levels > kMaxLevels ||
+            h_grid->log2_L0 < -100 || h_grid->log2_L0 > 100 ||
+            !(h_grid->x0 == h_grid->x0) || !(h_grid->y0 == h_grid->y0) || !(h_grid->z0 == h_grid->z0))
+            return SPH_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const float4 *pos = reinterpret_cast<const float4 *>(d_pos_h);
+    const int M = (int)ctx->M;
+    int rc;
+    if (h_grid) rc = launch_grid_set(*h_grid, ctx->grid, st);
+    else rc = launch_grid_auto(pos, n_gas, ctx->red, ctx->log2_M, ctx->grid, st);
+    if (rc) return rc;
+    // SP0: zero the per-bucket and per-level arrays
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)M, st));
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->hmax_cell, 0, sizeof(unsigned) * (size_t)M, st));
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_count, 0, sizeof(int) * kMaxLevels, st));
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
+    // SP1
+    if ((rc = launch_bin(pos, n_gas, ctx->grid, ctx->key, ctx->count, ctx->hmax_cell,
+                         ctx->lvl_count, ctx->lvl_hmax, st)))
+        return rc;
+    // SP2 + SP3
+    if ((rc = launch_scan_exclusive(ctx->count, M, ctx->start, ctx->block_sums, st))) return rc;
+    // SP4 + canonical order inside buckets
+    if ((rc = launch_scatter(ctx->key, n_gas, ctx->start, ctx->count, ctx->perm, st))) return rc;
+    if ((rc = launch_segsort_buckets(ctx->start, M, ctx->perm, ctx->tmp, ctx->long_list,
+                                     ctx->long_count, st)))
+        return rc;
+    if ((rc = launch_gather_float4(pos, ctx->perm, n_gas, ctx->pos_h_s, st))) return rc;
+    ctx->n_sorted = n_gas;
+    ctx->nb_built = 0;
+    if (d_key_out && n_gas)
+        SPH_CUDA_TRY(cudaMemcpyAsync(d_key_out, ctx->key, sizeof(int) * (size_t)n_gas,
+                                     cudaMemcpyDeviceToDevice, st));
+    if (d_cell_start_out)
+        SPH_CUDA_TRY(cudaMemcpyAsync(d_cell_start_out, ctx->start, sizeof(int) * ((size_t)M + 1),
+                                     cudaMemcpyDeviceToDevice, st));
+    if (d_perm_out && n_gas)
+        SPH_CUDA_TRY(cudaMemcpyAsync(d_perm_out, ctx->perm, sizeof(int) * (size_t)n_gas,
+                                     cudaMemcpyDeviceToDevice, st));
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour lists
+// ---------------------------------------------------------------------------
+
+extern "C" int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_start_out,
+                                   int32_t *d_nb_idx_out, int64_t out_capacity,
+                                   int64_t *h_needed, sph_stream_t stream) {
+    if (!ctx || n_gas != ctx->n_sorted || out_capacity < 0) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = n_gas;
+    NbArgs a;
+    a.pos_h_s = ctx->pos_h_s;
+    a.cell_start = ctx->start;
+    a.hmax_cell = ctx->hmax_cell;
+    a.lvl_count = ctx->lvl_count;
+    a.lvl_hmax = ctx->lvl_hmax;
+    a.grid = ctx->grid;
+    a.n = n;
+    a.own = ctx->own;
+    a.rev = ctx->rev;
+    a.nb_start = ctx->nb_start;
+    a.nb_idx = ctx->nb_idx;
+    a.capacity = ctx->capacity;
+    a.flags = ctx->flags;
+    int rc;
+    if (n > 0) SPH_CUDA_TRY(cudaMemsetAsync(ctx->rev, 0, sizeof(int) * (size_t)n, st));
+    if ((rc = launch_nb_count(a, st))) return rc;
+    if ((rc = launch_row_len(ctx->own, ctx->rev, n, ctx->row_len, st))) return rc;
+    if ((rc = launch_scan_exclusive(ctx->row_len, n, ctx->nb_start, ctx->block_sums, st))) return rc;
+    long long total = -1;
+    if (h_needed) {
+        int t = 0;
+        SPH_CUDA_TRY(cudaMemcpyAsync(&t, ctx->nb_start + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SPH_CUDA_TRY(cudaStreamSynchronize(st));
+        total = t;
+        *h_needed = total;
+        if (total > ctx->capacity) return SPH_ERR_NB_OVERFLOW;
+    }
+    if (n > 0) SPH_CUDA_TRY(cudaMemsetAsync(ctx->rev, 0, sizeof(int) * (size_t)n, st));
+    if ((rc = launch_nb_fill(a, st))) return rc;
+    if ((rc = launch_segsort_rows(ctx->nb_start, ctx->own, n, (int)ctx->capacity, ctx->nb_idx,
+                                  ctx->tmp, ctx->long_list, ctx->long_count, st)))
+        return rc;
+    ctx->nb_built = 1;
+    if (d_nb_start_out)
+        SPH_CUDA_TRY(cudaMemcpyAsync(d_nb_start_out, ctx->nb_start, sizeof(int) * ((size_t)n + 1),
+                                     cudaMemcpyDeviceToDevice, st));
+    if (d_nb_idx_out) {
+        if (total < 0) {
+            int t = 0;
+            SPH_CUDA_TRY(cudaMemcpyAsync(&t, ctx->nb_start + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SPH_CUDA_TRY(cudaStreamSynchronize(st));
+            total = t;
+        }
+        if (total <= out_capacity && total <= ctx->capacity && total > 0)
+            SPH_CUDA_TRY(cudaMemcpyAsync(d_nb_idx_out, ctx->nb_idx, sizeof(int) * (size_t)total,
+                                         cudaMemcpyDeviceToDevice, st));
+        else if (total > out_capacity)
+            return SPH_ERR_NB_OVERFLOW;
+    }
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// DC, HFC
+// ---------------------------------------------------------------------------
+
+extern "C" int sph_density(sph_ctx *ctx, int32_t n_gas, const float *d_mass, float *d_rho,
+                           float *d_h_next, sph_stream_t stream) {
+    if (!ctx || n_gas != ctx->n_sorted || !ctx->nb_built) return SPH_ERR_INVALID_ARG;
+    if (n_gas > 0 && (!d_mass || !d_rho || !d_h_next)) return SPH_ERR_INVALID_ARG;
+    return launch_density(ctx->pos_h_s, d_mass, ctx->perm, ctx->nb_start, ctx->nb_idx,
+                          (int)ctx->capacity, n_gas,
+                          ctx->params.sigma, ctx->rho_s, d_rho, d_h_next, ctx->mass_s,
+                          (cudaStream_t)stream);
+}
+
+extern "C" int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+                          const float *d_mass, float *d_acc_dedt, sph_stream_t stream) {
+    if (!ctx || n_gas != ctx->n_sorted || !ctx->nb_built) return SPH_ERR_INVALID_ARG;
+    if (n_gas > 0 && (!d_vel_e || !d_rho || !d_mass || !d_acc_dedt || !aligned16(d_vel_e) ||
+                      !aligned16(d_acc_dedt)))
+        return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HydroParams hp = hydro_params(ctx);
+    int rc;
+    if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
+        return rc;
+    return launch_forces(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
+                         ctx->nb_idx, (int)ctx->capacity, n_gas, hp, reinterpret_cast<float4 *>(d_acc_dedt), st);
+}
+
+// ---------------------------------------------------------------------------
+// Whole steps
+// ---------------------------------------------------------------------------
+
+namespace {
+
+bool state_ok(const sph_ctx *ctx, const SphState *s) {
+    if (!s || s->n < 0 || s->n_gas < 0 || s->n_gas > s->n) return false;
+    if (s->n_gas > 0 && (!ctx || s->n_gas > ctx->n_max)) return false;
+    if (s->n > 0 && (!s->r || !s->v || !s->v_save || !s->mass || !s->pos_m || !s->grav))
+        return false;
+    if (s->n_gas > 0 && (!s->e || !s->e_save || !s->h || !s->pos_h || !s->vel_e || !s->rho ||
+                         !s->acc_hyd))
+        return false;
+    return true;
+}
+
+int rhs_gas(sph_ctx *ctx, SphState *s, cudaStream_t st) {
+    int rc;
+    if ((rc = sph_bin_and_sort(ctx, s->pos_h, s->n_gas, nullptr, nullptr, nullptr, nullptr,
+                               (sph_stream_t)st)))
+        return rc;
+    if ((rc = sph_build_neighbors(ctx, s->n_gas, nullptr, nullptr, 0, nullptr, (sph_stream_t)st)))
+        return rc;
+    return sph_density(ctx, s->n_gas, s->mass, s->rho, s->h, (sph_stream_t)st);
+}
+
+}  // namespace
+
+extern "C" int sph_rhs_initial(sph_ctx *ctx, SphState *s, sph_stream_t stream) {
+    if (!state_ok(ctx, s)) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = integrate_step(SPH_EMIT, 0.0, s->n, s->n_gas, s->r, s->v, s->e, s->v_save, s->e_save,
+                             s->acc_hyd, s->grav, s->mass, s->h, s->pos_m, s->pos_h, s->vel_e,
+                             stream)))
+        return rc;
+    if (s->n_gas > 0 && (rc = rhs_gas(ctx, s, st))) return rc;
+    if ((rc = pp_gravity(s->pos_m, s->n, ctx ? ctx->params.G : 1.0f, ctx ? ctx->params.eps : 0.0f,
+                         s->grav, s->grav_flags, stream)))
+        return rc;
+    if (s->n_gas > 0 &&
+        (rc = sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, stream)))
+        return rc;
+    s->fresh = 1;
+    return SPH_OK;
+}
+
+namespace {
+
+struct StageMark {
+    void **ev;
+    cudaStream_t st;
+    int begin(int k) const {
+        if (ev) SPH_CUDA_TRY(cudaEventRecord((cudaEvent_t)ev[2 * k], st));
+        return SPH_OK;
+    }
+    int end(int k) const {
+        if (ev) SPH_CUDA_TRY(cudaEventRecord((cudaEvent_t)ev[2 * k + 1], st));
+        return SPH_OK;
+    }
+};
+
+}  // namespace
+
+#define SPH_STAGE(k, expr)                  \
+    do {                                    \
+        if ((rc = mark.begin(k))) return rc; \
+        if ((rc = (expr))) return rc;        \
+        if ((rc = mark.end(k))) return rc;   \
+    } while (0)
+
+extern "C" int sph_step(sph_ctx *ctx, SphState *s, double dt, sph_stream_t stream) {
+    if (!state_ok(ctx, s) || !(dt == dt) || !ctx) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const StageMark mark{s->events, st};
+    const bool gas = s->n_gas > 0;
+    int rc;
+    // HFC at (r_n, v_n, e_n) on the lists and density of r_n
+    SPH_STAGE(SPH_STAGE_HFC_PRED,
+              (!s->fresh && gas) ? sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd,
+                                              stream)
+                                 : SPH_OK);
+    // SU predictor: v~, e~, r_{n+1}; FP32 copies with the next h
+    SPH_STAGE(SPH_STAGE_SU_PRED,
+              integrate_step(SPH_PREDICT, dt, s->n, s->n_gas, s->r, s->v, s->e, s->v_save,
+                             s->e_save, s->acc_hyd, s->grav, s->mass, s->h, s->pos_m, s->pos_h,
+                             s->vel_e, stream));
+    // SP, lists, DC at r_{n+1}
+    SPH_STAGE(SPH_STAGE_SP, gas ? sph_bin_and_sort(ctx, s->pos_h, s->n_gas, nullptr, nullptr,
+                                                   nullptr, nullptr, stream)
+                                : SPH_OK);
+    SPH_STAGE(SPH_STAGE_NB,
+              gas ? sph_build_neighbors(ctx, s->n_gas, nullptr, nullptr, 0, nullptr, stream) : SPH_OK);
+    SPH_STAGE(SPH_STAGE_DC, gas ? sph_density(ctx, s->n_gas, s->mass, s->rho, s->h, stream) : SPH_OK);
+    // GFC once per step at r_{n+1}
+    SPH_STAGE(SPH_STAGE_GFC, pp_gravity(s->pos_m, s->n, ctx->params.G, ctx->params.eps, s->grav,
+                                        s->grav_flags, stream));
+    // HFC at (r_{n+1}, v~, e~)
+    SPH_STAGE(SPH_STAGE_HFC_CORR,
+              gas ? sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, stream) : SPH_OK);
+    // SU corrector
+    SPH_STAGE(SPH_STAGE_SU_CORR,
+              integrate_step(SPH_CORRECT, dt, s->n, s->n_gas, s->r, s->v, s->e, s->v_save,
+                             s->e_save, s->acc_hyd, s->grav, s->mass, s->h, nullptr, nullptr,
+                             s->vel_e, stream));
+    s->fresh = 0;
+    return SPH_OK;
+}

@@ -1,0 +1,119 @@
+// common.cuh -- shared device helpers of the sm_103a SPH library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sphgb.h"
+
+namespace sphgb {
+
+constexpr int kCellMax = 2097151;          // 2^21 - 1 cells per axis
+constexpr int kMaxLevels = 32;
+constexpr unsigned long long kLevelSalt = 0x9E3779B97F4A7C15ull;
+
+// Grid of the sorting stage as the kernels read it (device copy).
+struct GridDev {
+    float x0, y0, z0;
+    int log2_L0;
+    int n_levels;
+    int log2_M;
+};
+
+// 2^e as FP32 for e in [-126, 127], built from its bits (exact).
+__device__ __forceinline__ float pow2f(int e) {
+    return __uint_as_float((unsigned)(e + 127) << 23);
+}
+
+// Level of a smoothing length: smallest l >= 0 with h <= L0 * 2^l, clamped.
+// Integer arithmetic on the FP32 bits of the exact quotient h / L0.
+__device__ __forceinline__ int level_of(float h, int log2_L0, int n_levels) {
+    float q = __fmul_rn(h, pow2f(-log2_L0));
+    int l;
+    if (!(q > 1.0f)) {
+        l = 0;
+    } else {
+        unsigned b = __float_as_uint(q);
+        int e = (int)((b >> 23) & 0xffu) - 127;
+        l = (b & 0x7fffffu) ? e + 1 : e;
+    }
+    return l < n_levels - 1 ? l : n_levels - 1;
+}
+
+// Cell coordinate floor((x - x0) * inv_c), clamped to [0, kCellMax]; NaN -> 0.
+// Separate rounded subtract and multiply (no contraction) so the host-side
+// definition of the grid reproduces it bit for bit.
+__device__ __forceinline__ int cell_of(float x, float x0, float inv_c) {
+    float u = __fmul_rn(__fsub_rn(x, x0), inv_c);
+    if (!(u > 0.0f)) return 0;
+    if (u >= (float)kCellMax) return kCellMax;
+    return (int)u;
+}
+
+// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
+__device__ __forceinline__ unsigned long long spread3(unsigned v) {
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2_M) {
+    unsigned long long m = spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) |
+                           (spread3((unsigned)cz) << 2);
+    unsigned long long k = m + (unsigned long long)l * kLevelSalt;
+    return (int)(k & ((1ull << log2_M) - 1ull));
+}
+
+// FP32 neighbour predicate: ((dx*dx + dy*dy) + dz*dz) < (h_i + h_j)^2,
+// every operation rounded separately.
+__device__ __forceinline__ bool nb_pred(float4 a, float4 b) {
+    float dx = __fsub_rn(a.x, b.x);
+    float dy = __fsub_rn(a.y, b.y);
+    float dz = __fsub_rn(a.z, b.z);
+    float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    float s = __fadd_rn(a.w, b.w);
+    return r2 < __fmul_rn(s, s);
+}
+
+// Ordered-integer image of a float for atomicMin/atomicMax.
+__device__ __forceinline__ unsigned float_to_ordered(float f) {
+    unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Kahan-compensated FP32 accumulation.
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.0f; c = 0.0f; }
+    __device__ __forceinline__ void add(float x) {
+        float y = __fsub_rn(x, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s; }
+};
+
+__device__ __forceinline__ void set_flag(int *flags, int bit) {
+    if (flags) atomicOr(flags, bit);
+}
+
+// Count kernel launches made by the library (read through sph_launch_count).
+void note_launch(int k = 1);
+}  // namespace sphgb
+
+// Host-side launch helpers shared by the translation units.
+#define SPH_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return SPH_ERR_CUDA;          \
+    } while (0)
+
+#define SPH_LAUNCH_CHECK() SPH_CUDA_TRY(cudaGetLastError())

@@ -1,0 +1,404 @@
+// gravity.cu -- direct particle-particle gravity (GFC, Eq. 4 of the paper,
+// Plummer-softened reading) on the FP32 pipe of sm_103a.
+//
+// g_i = -G sum_{j != i} m_j (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^(3/2)
+//
+// Design (the paper stages j-tiles through shared memory on Kepler; this is
+// the GB300 form of the same idea):
+//  * each CTA owns 256 * R target particles i (R per thread, kept in
+//    registers) and streams source tiles of TJ float4 (x, y, z, m) into
+//    shared memory with 1-D TMA bulk copies (cp.async.bulk), double-buffered
+//    and completed through mbarriers (waits bounded in time);
+//  * the inner loop is 3 FADD + 3 FFMA + 1 MUFU.RSQ + 3 FMUL + 3 FFMA per
+//    interaction on one broadcast shared-memory load per source and thread;
+//  * per-tile partial sums are folded into Kahan-compensated running sums;
+//  * when there are too few target blocks to fill 152 SMs, the source range
+//    is split over the S CTAs of a thread-block cluster and the S partial
+//    sums are combined in a fixed order through distributed shared memory, so
+//    the kernel needs no global scratch and stays deterministic.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sphgb {
+
+constexpr int GR_THREADS = 256;
+constexpr int GR_TJ = 1024;                        // sources per tile
+constexpr int GR_SMEM = 2 * GR_TJ * 16 + 64;       // two tiles + two mbarriers
+
+__device__ int g_grav_flags;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after ~2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes,
+                                         unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int R, bool POT, bool GUARD, bool KAHAN>
+__global__ void __launch_bounds__(GR_THREADS)
+pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, float G, float eps2,
+                  float4 *__restrict__ out) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *tiles = reinterpret_cast<float4 *>(smem);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + 2 * GR_TJ * 16);
+    const int tid = threadIdx.x;
+    const int rank = blockIdx.x % S;   // cluster dims (S, 1, 1): rank == ctarank
+    const int i0 = (blockIdx.x / S) * (GR_THREADS * R);
+    const int t_begin = (int)((long long)n_tiles * rank / S);
+    const int t_end = (int)((long long)n_tiles * (rank + 1) / S);
+    const int my_tiles = t_end - t_begin;
+
+    float xi[R], yi[R], zi[R];
+    Kahan ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        int i = i0 + tid + k * GR_THREADS;
+        float4 p = i < n ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xi[k] = p.x; yi[k] = p.y; zi[k] = p.z;
+        ax[k].init(); ay[k].init(); az[k].init(); ph[k].init();
+    }
+
+    const unsigned bar0 = smem_u32(&bars[0]);
+    const unsigned tiles0 = smem_u32(tiles);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int b = 0; b < 2 && b < my_tiles; ++b) {
+            int j0 = (t_begin + b) * GR_TJ;
+            unsigned bytes = (unsigned)min(GR_TJ, n - j0) * 16u;
+            mbar_expect_tx(bar0 + 8 * b, bytes);
+            bulk_g2s(tiles0 + b * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * b);
+        }
+    }
+
+    bool failed = false;
+    for (int t = 0; t < my_tiles; ++t) {
+        const int buf = t & 1;
+        bool ok = mbar_wait_bounded(bar0 + 8 * buf, (unsigned)((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        const int cnt = min(GR_TJ, n - (t_begin + t) * GR_TJ);
+        const float4 *tb = tiles + buf * GR_TJ;
+        float sx[R], sy[R], sz[R], sp[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) { sx[k] = 0.f; sy[k] = 0.f; sz[k] = 0.f; sp[k] = 0.f; }
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 q = tb[j];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                float dx = q.x - xi[k];
+                float dy = q.y - yi[k];
+                float dz = q.z - zi[k];
+                float r2 = fmaf(dx, dx, eps2);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float inv = rsqrt_mufu(r2);
+                if (GUARD) inv = r2 > 0.f ? inv : 0.f;
+                float s = q.w * inv;
+                float s3 = (s * inv) * inv;
+                sx[k] = fmaf(s3, dx, sx[k]);
+                sy[k] = fmaf(s3, dy, sy[k]);
+                sz[k] = fmaf(s3, dz, sz[k]);
+                if (POT) sp[k] += s;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (KAHAN) {
+                ax[k].add(sx[k]); ay[k].add(sy[k]); az[k].add(sz[k]);
+                if (POT) ph[k].add(sp[k]);
+            } else {
+                ax[k].s += sx[k]; ay[k].s += sy[k]; az[k].s += sz[k];
+                if (POT) ph[k].s += sp[k];
+            }
+        }
+        __syncthreads();   // every thread is done reading this buffer
+        if (tid == 0 && t + 2 < my_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            int j0 = (t_begin + t + 2) * GR_TJ;
+            unsigned bytes = (unsigned)min(GR_TJ, n - j0) * 16u;
+            mbar_expect_tx(bar0 + 8 * buf, bytes);
+            bulk_g2s(tiles0 + buf * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * buf);
+        }
+    }
+    if (failed && tid == 0) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
+
+    // self term of the potential: the loop included j == i with |dr| = 0
+    const float self_inv = GUARD ? 0.f : rsqrt_mufu(eps2);
+
+    if (S == 1) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            int i = i0 + tid + k * GR_THREADS;
+            if (i < n) {
+                float m_i = pos[i].w;
+                float pot = POT ? -G * ((ph[k].s - ph[k].c) - m_i * self_inv) : 0.f;
+                out[i] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
+                                     G * (az[k].s - az[k].c), pot);
+            }
+        }
+        return;
+    }
+
+    // Cluster combine: partial sums of the S source ranges meet in shared
+    // memory; rank r sums a 1/S slice of the targets over ranks 0..S-1.
+    cg::cluster_group cluster = cg::this_cluster();
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(smem);   // [4][GR_THREADS * R]
+    constexpr int NB = GR_THREADS * R;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        int q = tid + k * GR_THREADS;
+        red[0 * NB + q] = ax[k].s - ax[k].c;
+        red[1 * NB + q] = ay[k].s - ay[k].c;
+        red[2 * NB + q] = az[k].s - az[k].c;
+        red[3 * NB + q] = POT ? ph[k].s - ph[k].c : 0.f;
+    }
+    cluster.sync();
+    const int per = NB / S;
+    for (int q = rank * per + tid; q < (rank + 1) * per; q += GR_THREADS) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int r = 0; r < S; ++r) {
+            const float *peer = cluster.map_shared_rank(red, r);
+            a0 += peer[0 * NB + q];
+            a1 += peer[1 * NB + q];
+            a2 += peer[2 * NB + q];
+            a3 += peer[3 * NB + q];
+        }
+        int i = i0 + q;
+        if (i < n) {
+            float m_i = pos[i].w;
+            out[i] = make_float4(G * a0, G * a1, G * a2, POT ? -G * (a3 - m_i * self_inv) : 0.f);
+        }
+    }
+    cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Host side: pick R (targets per thread) and S (cluster split of the sources)
+// by a wave-quantisation cost model over the measured occupancy.
+// ---------------------------------------------------------------------------
+
+using GravKernel = void (*)(const float4 *, int, int, int, float, float, float4 *);
+
+template <int R>
+static GravKernel pick_kernel(bool pot, bool guard, bool kahan) {
+    if (pot) {
+        if (guard) return kahan ? pp_gravity_kernel<R, true, true, true> : pp_gravity_kernel<R, true, true, false>;
+        return kahan ? pp_gravity_kernel<R, true, false, true> : pp_gravity_kernel<R, true, false, false>;
+    }
+    if (guard) return kahan ? pp_gravity_kernel<R, false, true, true> : pp_gravity_kernel<R, false, true, false>;
+    return kahan ? pp_gravity_kernel<R, false, false, true> : pp_gravity_kernel<R, false, false, false>;
+}
+
+static GravKernel kernel_for(int R, bool pot, bool guard, bool kahan) {
+    switch (R) {
+        case 1: return pick_kernel<1>(pot, guard, kahan);
+        case 2: return pick_kernel<2>(pot, guard, kahan);
+        default: return pick_kernel<4>(pot, guard, kahan);
+    }
+}
+
+struct GravPlan {
+    int R, S;
+};
+
+static int g_num_sms = 0;
+
+static int slots_for(GravKernel k, int S) {
+    if (S == 1) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, GR_THREADS, GR_SMEM) !=
+            cudaSuccess)
+            return 0;
+        return occ * g_num_sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S * 64, 1, 1);
+    cfg.blockDim = dim3(GR_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = GR_SMEM;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = S;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return clusters * S;
+}
+
+static GravPlan plan_gravity(int n, bool pot, bool guard, bool kahan) {
+    const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
+    GravPlan best{4, 1};
+    double best_cost = 1e300;
+    const int Rs[3] = {4, 2, 1};
+    const int Ss[5] = {1, 2, 4, 8, 16};
+    for (int R : Rs) {
+        GravKernel k = kernel_for(R, pot, guard, kahan);
+        const double per_int = 13.0 + 1.5 / R;   // issue slots per interaction
+        const long long nib = (n + GR_THREADS * R - 1) / (GR_THREADS * R);
+        for (int S : Ss) {
+            if (S > 1 && S > n_tiles) break;
+            int slots = slots_for(k, S);
+            if (slots <= 0) continue;
+            long long units = nib * S;
+            long long waves = (units + slots - 1) / slots;
+            double resident = (double)std::min<long long>(units, slots) / g_num_sms;
+            double per_cta = (double)GR_THREADS * R * ((double)n / S) * per_int;
+            double cost = (double)waves * resident * per_cta * (1.0 + 0.002 * S);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = GravPlan{R, S};
+            }
+        }
+    }
+    return best;
+}
+
+static std::once_flag g_grav_once;
+static int g_grav_init_status = SPH_OK;
+
+static void grav_init() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        g_grav_init_status = SPH_ERR_CUDA;
+        return;
+    }
+    const int Rs[3] = {1, 2, 4};
+    for (int R : Rs)
+        for (int f = 0; f < 8; ++f) {
+            GravKernel k = kernel_for(R, f & 1, f & 2, f & 4);
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess) {
+                cudaGetLastError();
+            }
+        }
+}
+
+}  // namespace sphgb
+
+using namespace sphgb;
+
+extern "C" int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
+                          int32_t flags, sph_stream_t stream) {
+    if (n < 0 || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
+    if (n == 0) return SPH_OK;
+    if (!d_pos_m || !d_acc_pot) return SPH_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_pos_m) & 15u) || (reinterpret_cast<uintptr_t>(d_acc_pot) & 15u))
+        return SPH_ERR_INVALID_ARG;
+    std::call_once(g_grav_once, grav_init);
+    if (g_grav_init_status != SPH_OK) return g_grav_init_status;
+
+    const bool pot = flags & SPH_GRAV_POTENTIAL;
+    const bool kahan = !(flags & SPH_GRAV_NO_KAHAN);
+    const float eps2 = eps * eps;
+    const bool guard = !(eps2 > 0.0f);
+    GravPlan p = plan_gravity(n, pot, guard, kahan);
+    GravKernel k = kernel_for(p.R, pot, guard, kahan);
+    const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
+    const int nib = (n + GR_THREADS * p.R - 1) / (GR_THREADS * p.R);
+
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nib * p.S), 1, 1);
+    cfg.blockDim = dim3(GR_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = GR_SMEM;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = p.S;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = p.S > 1 ? 1 : 0;
+    SPH_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, reinterpret_cast<const float4 *>(d_pos_m), (int)n,
+                                    n_tiles, p.S, G, eps2, reinterpret_cast<float4 *>(d_acc_pot)));
+    note_launch();
+    return SPH_OK;
+}
+
+extern "C" int pp_gravity_status(sph_stream_t stream, int32_t *h_flags) {
+    if (!h_flags) return SPH_ERR_INVALID_ARG;
+    SPH_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int v = 0, zero = 0;
+    SPH_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_grav_flags, sizeof(int)));
+    SPH_CUDA_TRY(cudaMemcpyToSymbol(g_grav_flags, &zero, sizeof(int)));
+    *h_flags = v;
+    return v ? SPH_ERR_DEVICE : SPH_OK;
+}
+
+// Launch plan exposed for tests and the bench's roofline accounting.
+extern "C" int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t *h_S) {
+    if (n <= 0 || !h_R || !h_S) return SPH_ERR_INVALID_ARG;
+    std::call_once(g_grav_once, grav_init);
+    if (g_grav_init_status != SPH_OK) return g_grav_init_status;
+    GravPlan p = plan_gravity(n, flags & SPH_GRAV_POTENTIAL, false, !(flags & SPH_GRAV_NO_KAHAN));
+    *h_R = p.R;
+    *h_S = p.S;
+    return SPH_OK;
+}

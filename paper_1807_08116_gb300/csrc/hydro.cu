@@ -1,0 +1,165 @@
+// hydro.cu -- the SPH sums of the paper: density DC (Eq. 7 with the cubic
+// spline of Eq. 8) and the hydrodynamic force HFC (Eqs. 10-11 with the
+// pressure kernel of Eq. 9 and Monaghan's viscosity, Sect. 2.2).
+//
+// Both run in sorted (bucket) order over the CSR neighbour lists: one thread
+// per row, FP32 arithmetic, Kahan-compensated sums, results scattered back
+// to the caller's order through perm.  The working set of a row's
+// neighbours (16-48 bytes each) is read through L1/L2; the lists themselves
+// stream from HBM.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sphgb {
+
+constexpr float kInvPi = 0.318309886183790671538f;
+
+// Cubic spline of Eq. 8 without its 1/(pi h^3) factor.
+__device__ __forceinline__ float spline_shape(float xi) {
+    if (xi <= 1.0f) return fmaf(xi * xi, fmaf(0.75f, xi, -1.5f), 1.0f);
+    float t = 2.0f - xi;
+    return xi < 2.0f ? 0.25f * t * t * t : 0.0f;
+}
+
+__global__ void __launch_bounds__(128)
+density_kernel(const float4 *__restrict__ pos_h_s, const float *__restrict__ mass,
+               const int *__restrict__ perm, const int *__restrict__ nb_start,
+               const int *__restrict__ nb_idx, int cap, int n, float sigma,
+               float *__restrict__ rho_s,
+               float *__restrict__ rho_out, float *__restrict__ h_next_out,
+               float *__restrict__ mass_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int oi = perm[i];
+    const float4 p = pos_h_s[i];
+    const float mi = mass[oi];
+    const float hi = p.w;
+    Kahan acc;
+    acc.init();
+    {
+        float ih = 1.0f / hi;
+        acc.add(mi * (ih * ih * ih) * kInvPi);   // self term m_i W(0, h_i)
+    }
+    // rows are clipped to the list capacity (an overflowed build is flagged)
+    const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+    for (int k = b; k < e; ++k) {
+        const int j = nb_idx[k];
+        if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
+        const float4 q = pos_h_s[j];
+        const float mj = mass[perm[j]];
+        float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float hij = 0.5f * (hi + q.w);
+        float ih = 1.0f / hij;
+        acc.add(mj * (ih * ih * ih) * kInvPi * spline_shape(r * ih));
+    }
+    const float rho = acc.value();
+    rho_s[i] = rho;
+    mass_s[i] = mi;
+    rho_out[oi] = rho;
+    h_next_out[oi] = sigma * cbrtf(mi / rho);
+}
+
+// Sorted working copies for HFC: vel_s = (vx, vy, vz, e); aux_s = (m, rho,
+// P = p / rho^2 = (gamma - 1) e / rho, c = sqrt(gamma (gamma - 1) e), 0 if e < 0).
+__global__ void hydro_prep_kernel(const float4 *__restrict__ vel_e, const float *__restrict__ rho,
+                                  const float *__restrict__ mass, const int *__restrict__ perm,
+                                  int n, HydroParams hp, float4 *__restrict__ vel_s,
+                                  float4 *__restrict__ aux_s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int o = perm[j];
+    const float4 v = vel_e[o];
+    const float r = rho[o];
+    const float gm1 = hp.gamma - 1.0f;
+    const float P = gm1 * v.w / r;
+    const float c = v.w >= 0.0f ? sqrtf(hp.gamma * gm1 * v.w) : 0.0f;
+    vel_s[j] = v;
+    aux_s[j] = make_float4(mass[o], r, P, c);
+}
+
+__global__ void __launch_bounds__(128)
+forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
+              const float4 *__restrict__ aux_s, const int *__restrict__ perm,
+              const int *__restrict__ nb_start, const int *__restrict__ nb_idx, int cap, int n,
+              HydroParams hp, float4 *__restrict__ acc_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = pos_h_s[i];
+    const float4 v = vel_s[i];
+    const float4 ai = aux_s[i];
+    // dW_p/dxi = -(45 / (64 pi)) h^-3 (2 - xi)^2  (derivative of Eq. 9)
+    const float kdw = -45.0f / 64.0f * kInvPi;
+    Kahan ax, ay, az, de;
+    ax.init(); ay.init(); az.init(); de.init();
+    // rows are clipped to the list capacity (an overflowed build is flagged)
+    const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+    for (int k = b; k < e; ++k) {
+        const int j = nb_idx[k];
+        if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
+        const float4 q = pos_h_s[j];
+        const float4 w = vel_s[j];
+        const float4 aj = aux_s[j];
+        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        const float dvx = v.x - w.x, dvy = v.y - w.y, dvz = v.z - w.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float r = sqrtf(r2);
+        const float hij = 0.5f * (p.w + q.w);
+        const float ih = 1.0f / hij;
+        const float t = fmaxf(2.0f - r * ih, 0.0f);
+        // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
+        const float f = r > 0.0f ? kdw * (ih * ih * ih) * t * t * ih / r : 0.0f;
+        const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+        float nu = 0.0f;
+        if (rv < 0.0f) {
+            const float mu = hij * rv / fmaf(hp.eta * hij, hij, r2);
+            const float rho_ij = 0.5f * (ai.y + aj.y);
+            const float c_ij = 0.5f * (ai.w + aj.w);
+            nu = mu * fmaf(hp.beta, mu, -hp.alpha * c_ij) / rho_ij;
+        }
+        const float Pi = ai.z + aj.z + nu;
+        const float g = aj.x * Pi * f;   // m_j Pi_ij f
+        ax.add(-g * dx);
+        ay.add(-g * dy);
+        az.add(-g * dz);
+        de.add(0.5f * g * fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz)));
+    }
+    acc_out[perm[i]] = make_float4(ax.value(), ay.value(), az.value(), de.value());
+}
+
+int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, const int *nb_start,
+                   const int *nb_idx, int cap, int n, float sigma, float *rho_s, float *rho_out,
+                   float *h_next_out, float *mass_s, cudaStream_t st) {
+    if (n > 0) {
+        density_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, mass, perm, nb_start, nb_idx, cap,
+                                                        n, sigma, rho_s, rho_out, h_next_out, mass_s);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
+                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st) {
+    if (n > 0) {
+        hydro_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(vel_e, rho, mass, perm, n, hp, vel_s,
+                                                           aux_s);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
+                  const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
+                  HydroParams hp, float4 *acc_out, cudaStream_t st) {
+    if (n > 0) {
+        forces_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start,
+                                                       nb_idx, cap, n, hp, acc_out);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+}  // namespace sphgb

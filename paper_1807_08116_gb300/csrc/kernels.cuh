@@ -1,0 +1,58 @@
+// kernels.cuh -- host-side launchers shared between translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace sphgb {
+
+// sort.cu
+int launch_scan_exclusive(const int *in, int n, int *out, int *block_sums, cudaStream_t st);
+int scan_block_count(long long n);
+int launch_segsort_buckets(const int *start, int M, int *data, int *tmp, int *long_list,
+                           int *long_count, cudaStream_t st);
+int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int *data, int *tmp,
+                        int *long_list, int *long_count, cudaStream_t st);
+int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
+                     cudaStream_t st);
+int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st);
+int launch_bin(const float4 *pos_h, int n, const GridDev *grid, int *key, int *count,
+               unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st);
+int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
+int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st);
+void grid_reset_red(unsigned *red, const unsigned *v, cudaStream_t st);
+
+// neighbors.cu
+struct NbArgs {
+    const float4 *pos_h_s;   // sorted (x, y, z, h)
+    const int *cell_start;   // [M + 1]
+    const unsigned *hmax_cell;
+    const int *lvl_count;    // [kMaxLevels]
+    const unsigned *lvl_hmax;
+    const GridDev *grid;
+    int n;
+    int *own;                // [n] own-search count
+    int *rev;                // [n] reverse count / cursor
+    const int *nb_start;     // [n + 1]
+    int *nb_idx;
+    long long capacity;
+    int *flags;
+};
+int launch_nb_count(const NbArgs &a, cudaStream_t st);
+int launch_nb_fill(const NbArgs &a, cudaStream_t st);
+int launch_row_len(const int *own, const int *rev, int n, int *row_len, cudaStream_t st);
+
+// hydro.cu
+struct HydroParams {
+    float gamma, alpha, beta, eta, sigma;
+};
+int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, const int *nb_start,
+                   const int *nb_idx, int cap, int n, float sigma, float *rho_s, float *rho_out,
+                   float *h_next_out, float *mass_s, cudaStream_t st);
+int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
+                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st);
+int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
+                  const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
+                  HydroParams hp,
+                  float4 *acc_out, cudaStream_t st);
+
+}  // namespace sphgb

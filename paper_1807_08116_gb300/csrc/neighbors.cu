@@ -1,0 +1,125 @@
+// neighbors.cu -- per-particle neighbour lists over the multi-level hashed
+// grid built by the sorting stage.  The paper's DC and HFC kernels walk the
+// cells around each particle with indexPC, CellSPH and hmaxCell (Sect. 3);
+// here the walk is done once per step and its result is stored as CSR lists,
+// which density and both force evaluations then stream.
+//
+// j is a neighbour of i (j != i) iff, in FP32, ((dx*dx + dy*dy) + dz*dz) <
+// (h_i + h_j)^2, i.e. |r_ij| < 2 h_ij, the support of W and W_p (Eqs. 8-9).
+//
+// Search: particle i (level l_i) visits only levels l >= l_i.  On level l
+// every particle has h <= hmax_l, so all its possible neighbours lie in the
+// cells covering [x_i - R, x_i + R] with R = h_i + hmax_l (widened by a few
+// ulps so that FP32 rounding of the predicate can never reach outside).
+// Because h_i <= L0 2^l_i <= L0 2^l and hmax_l <= L0 2^l, this box spans at
+// most 5 cells per axis.  A pair on the same level is found from both ends;
+// a pair with l_j > l_i is found only by i, which appends j to its own row
+// and i to j's row ("reverse" part, atomic cursor).  Buckets are shared by
+// distinct cells through the hash; each candidate is accepted only if its own
+// level and cell equal the probed ones, so no pair is counted twice.
+// Rows are [own part in search order | reverse part sorted ascending].
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sphgb {
+
+__device__ __forceinline__ void search_box(float x, float R, float x0, float inv_c, int &lo,
+                                           int &hi) {
+    // R' >= R (1 + 16 ulp) + |x| 4 ulp: covers every FP32 rounding path of the
+    // predicate and of x +- R'
+    float m = fmaf(R, 1.0f + 3.814697265625e-06f, fmaf(fabsf(x), 9.5367431640625e-07f, 1e-30f));
+    lo = cell_of(__fsub_rn(x, m), x0, inv_c);
+    hi = cell_of(__fadd_rn(x, m), x0, inv_c);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const GridDev g = *a.grid;
+    const float4 p = a.pos_h_s[i];
+    const int li = level_of(p.w, g.log2_L0, g.n_levels);
+    int cnt = 0;
+    long long base = 0;
+    if (FILL) base = a.nb_start[i];
+    for (int l = li; l < g.n_levels; ++l) {
+        if (a.lvl_count[l] == 0) continue;
+        const float R = __fadd_rn(p.w, __uint_as_float(a.lvl_hmax[l]));
+        if (!(R >= 0.0f)) continue;
+        const float inv_c = pow2f(-g.log2_L0 - l);
+        int lx, hx, ly, hy, lz, hz;
+        search_box(p.x, R, g.x0, inv_c, lx, hx);
+        search_box(p.y, R, g.y0, inv_c, ly, hy);
+        search_box(p.z, R, g.z0, inv_c, lz, hz);
+        long long ncell = (long long)(hx - lx + 1) * (hy - ly + 1) * (hz - lz + 1);
+        if (ncell > (1ll << 24)) {
+            set_flag(a.flags, SPH_FLAG_SEARCH_WIDE);
+            continue;
+        }
+        for (int cz = lz; cz <= hz; ++cz)
+            for (int cy = ly; cy <= hy; ++cy)
+                for (int cx = lx; cx <= hx; ++cx) {
+                    const int k = bucket_of(cx, cy, cz, l, g.log2_M);
+                    const int s = a.cell_start[k], e = a.cell_start[k + 1];
+                    for (int j = s; j < e; ++j) {
+                        if (j == i) continue;
+                        const float4 q = a.pos_h_s[j];
+                        if (level_of(q.w, g.log2_L0, g.n_levels) != l) continue;
+                        if (cell_of(q.x, g.x0, inv_c) != cx || cell_of(q.y, g.y0, inv_c) != cy ||
+                            cell_of(q.z, g.z0, inv_c) != cz)
+                            continue;
+                        if (!nb_pred(p, q)) continue;
+                        if (FILL) {
+                            long long w = base + cnt;
+                            if (w < a.capacity) a.nb_idx[w] = j;
+                            else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+                            if (l > li) {
+                                int pos = atomicAdd(&a.rev[j], 1);
+                                long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
+                                if (wr < a.capacity) a.nb_idx[wr] = i;
+                                else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+                            }
+                        } else if (l > li) {
+                            atomicAdd(&a.rev[j], 1);
+                        }
+                        ++cnt;
+                    }
+                }
+    }
+    if (!FILL) a.own[i] = cnt;
+}
+
+__global__ void row_len_kernel(const int *__restrict__ own, const int *__restrict__ rev, int n,
+                               int *__restrict__ len) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) len[i] = own[i] + rev[i];
+}
+
+int launch_nb_count(const NbArgs &a, cudaStream_t st) {
+    if (a.n > 0) {
+        nb_kernel<false><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_nb_fill(const NbArgs &a, cudaStream_t st) {
+    if (a.n > 0) {
+        nb_kernel<true><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_row_len(const int *own, const int *rev, int n, int *row_len, cudaStream_t st) {
+    if (n > 0) {
+        row_len_kernel<<<(n + 255) / 256, 256, 0, st>>>(own, rev, n, row_len);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+}  // namespace sphgb

@@ -1,0 +1,416 @@
+// sort.cu -- the sorting stage SP of the paper (Sect. 3): binning of the gas
+// particles into buckets of a multi-level hashed grid, bucket counts, a
+// block-cascaded exclusive prefix sum, the counting-sort scatter, and the
+// canonicalisation that makes the scatter stable (ascending original index
+// inside a bucket) and so deterministic.
+//
+// The paper's SP1 counts with global atomics, SP2 scans inside a CUDA block
+// in shared memory and adds each block total into every later block with
+// atomics (O(G^2) adds), SP3 adds the block offsets, SP4 scatters with an
+// atomic cursor.  Here SP2/SP3 become a reduce-then-scan cascade (warp
+// shuffles, then shared memory, then one pass over block totals) with no
+// spin-waits, and SP4's arbitrary within-bucket order is repaired by a
+// segmented sort of each bucket.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sphgb {
+
+// ---------------------------------------------------------------------------
+// Automatic grid: origin floor(min x) - 1 per axis, L0 = 2^ceil(log2 min h),
+// n_levels = 1 + ceil(log2(max h / L0)) (at most 24).
+// red[0..2] ordered-min of x, y, z; red[3] ordered-min of h; red[4] ordered-max of h.
+// ---------------------------------------------------------------------------
+
+__global__ void grid_reduce_kernel(const float4 *__restrict__ pos_h, int n, unsigned *red) {
+    __shared__ unsigned s[5];
+    if (threadIdx.x < 5) s[threadIdx.x] = threadIdx.x == 4 ? 0u : 0xffffffffu;
+    __syncthreads();
+    unsigned mx = 0xffffffffu, my = 0xffffffffu, mz = 0xffffffffu, mh = 0xffffffffu, Mh = 0u;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 p = pos_h[i];
+        if (p.x == p.x && fabsf(p.x) < 3.0e38f) mx = min(mx, float_to_ordered(p.x));
+        if (p.y == p.y && fabsf(p.y) < 3.0e38f) my = min(my, float_to_ordered(p.y));
+        if (p.z == p.z && fabsf(p.z) < 3.0e38f) mz = min(mz, float_to_ordered(p.z));
+        if (p.w > 0.0f && p.w < 3.0e38f) {
+            mh = min(mh, float_to_ordered(p.w));
+            Mh = max(Mh, float_to_ordered(p.w));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = min(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
+        mz = min(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+        mh = min(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+        Mh = max(Mh, __shfl_xor_sync(0xffffffffu, Mh, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s[0], mx); atomicMin(&s[1], my); atomicMin(&s[2], mz);
+        atomicMin(&s[3], mh); atomicMax(&s[4], Mh);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMin(&red[0], s[0]); atomicMin(&red[1], s[1]); atomicMin(&red[2], s[2]);
+        atomicMin(&red[3], s[3]); atomicMax(&red[4], s[4]);
+    }
+}
+
+__device__ __forceinline__ int ceil_log2_pos(float v) {
+    // ceil(log2(v)) for finite v > 0, exact from the FP32 bits
+    unsigned b = __float_as_uint(v);
+    int e = (int)((b >> 23) & 0xffu);
+    unsigned mant = b & 0x7fffffu;
+    if (e == 0) {   // subnormal: v = mant * 2^-149
+        int lz = __clz(mant) - 8;   // leading zeros within 23 bits
+        int top = 22 - lz;          // index of highest set bit
+        int fl = top - 149;
+        return (mant & ((1u << top) - 1u)) ? fl + 1 : fl;
+    }
+    int fl = e - 127;
+    return mant ? fl + 1 : fl;
+}
+
+__global__ void grid_finalize_kernel(const unsigned *red, int log2_M, GridDev *grid) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float mins[3];
+    for (int d = 0; d < 3; ++d) {
+        float v = red[d] == 0xffffffffu ? 0.0f : ordered_to_float(red[d]);
+        mins[d] = floorf(v) - 1.0f;
+    }
+    float hmin = red[3] == 0xffffffffu ? 1.0f : ordered_to_float(red[3]);
+    float hmax = red[4] == 0u ? hmin : ordered_to_float(red[4]);
+    int l0 = ceil_log2_pos(hmin);
+    l0 = max(-100, min(100, l0));
+    int top = ceil_log2_pos(hmax) - l0;   // levels above L0 needed for hmax
+    int nl = 1 + max(0, top);
+    nl = min(nl, 24);
+    grid->x0 = mins[0];
+    grid->y0 = mins[1];
+    grid->z0 = mins[2];
+    grid->log2_L0 = l0;
+    grid->n_levels = nl;
+    grid->log2_M = log2_M;
+}
+
+__global__ void grid_set_kernel(GridDev g, GridDev *grid) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *grid = g;
+}
+
+// ---------------------------------------------------------------------------
+// SP1: bucket of each particle, bucket counts, per-bucket max h, per-level
+// count and max h.
+// ---------------------------------------------------------------------------
+
+__global__ void bin_kernel(const float4 *__restrict__ pos_h, int n, const GridDev *__restrict__ gridp,
+                           int *__restrict__ key, int *__restrict__ count,
+                           unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
+                           unsigned *__restrict__ lvl_hmax) {
+    __shared__ int s_cnt[kMaxLevels];
+    __shared__ unsigned s_hmax[kMaxLevels];
+    if (threadIdx.x < kMaxLevels) {
+        s_cnt[threadIdx.x] = 0;
+        s_hmax[threadIdx.x] = 0u;
+    }
+    __syncthreads();
+    const GridDev g = *gridp;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float4 p = pos_h[i];
+        int l = level_of(p.w, g.log2_L0, g.n_levels);
+        float inv_c = pow2f(-g.log2_L0 - l);
+        int cx = cell_of(p.x, g.x0, inv_c);
+        int cy = cell_of(p.y, g.y0, inv_c);
+        int cz = cell_of(p.z, g.z0, inv_c);
+        int k = bucket_of(cx, cy, cz, l, g.log2_M);
+        key[i] = k;
+        atomicAdd(&count[k], 1);
+        unsigned hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
+        atomicMax(&hmax_cell[k], hb);
+        atomicAdd(&s_cnt[l], 1);
+        atomicMax(&s_hmax[l], hb);
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxLevels && s_cnt[threadIdx.x]) {
+        atomicAdd(&lvl_count[threadIdx.x], s_cnt[threadIdx.x]);
+        atomicMax(&lvl_hmax[threadIdx.x], s_hmax[threadIdx.x]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SP2/SP3: exclusive prefix sum, reduce-then-scan cascade.
+// out[0..n] with out[n] = total.  Each block covers SCAN_TILE inputs.
+// ---------------------------------------------------------------------------
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the
+// block total through *total.
+__device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int inc = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? s_warp[lane] : 0;
+        int wi = warp_incl_scan(w);
+        if (lane < nw) s_warp[lane] = wi - w;   // exclusive warp offsets
+        if (lane == nw - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    int res = inc - v + s_warp[warp];
+    *total = s_warp[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const int *__restrict__ in, int n,
+                                                                    int *__restrict__ block_sums) {
+    __shared__ int s_warp[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < n) v += in[base + q];
+    int total;
+    block_excl_scan(v, s_warp, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block totals, in place (any count).
+__global__ void __launch_bounds__(SCAN_THREADS) scan_blocks_kernel(int *block_sums, int nb) {
+    __shared__ int s_warp[33];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+        int idx = b0 + threadIdx.x;
+        int v = idx < nb ? block_sums[idx] : 0;
+        int total;
+        int ex = block_excl_scan(v, s_warp, &total);
+        if (idx < nb) block_sums[idx] = ex + carry;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_down_kernel(const int *__restrict__ in, int n,
+                                                                  const int *__restrict__ block_sums,
+                                                                  int *__restrict__ out) {
+    __shared__ int s_warp[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int vals[SCAN_ITEMS];
+    int v = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        vals[q] = base + q < n ? in[base + q] : 0;
+        v += vals[q];
+    }
+    int total;
+    int ex = block_excl_scan(v, s_warp, &total) + block_sums[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < n) out[base + q] = ex;
+        ex += vals[q];
+    }
+    if (base <= n && n < base + SCAN_ITEMS) out[n] = block_sums[blockIdx.x] + total;
+}
+
+// ---------------------------------------------------------------------------
+// SP4: scatter with an atomic cursor (count is driven back to zero), then a
+// per-bucket sort that makes the order inside every bucket ascending.
+// ---------------------------------------------------------------------------
+
+__global__ void scatter_kernel(const int *__restrict__ key, int n, const int *__restrict__ start,
+                               int *__restrict__ count, int *__restrict__ perm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = key[i];
+    int pos = atomicSub(&count[k], 1) - 1;
+    perm[start[k] + pos] = i;
+}
+
+constexpr int SEG_SMALL = 32;
+
+// One thread per segment [begin(s), end(s)): insertion sort when short,
+// otherwise queue the segment for the block-per-segment pass.
+template <class Seg>
+__global__ void segsort_small_kernel(Seg seg, int nseg, int *__restrict__ data,
+                                     int *__restrict__ long_list, int *__restrict__ long_count) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    int b = seg.begin(s), e = seg.end(s);
+    int len = e - b;
+    if (len <= 1) return;
+    if (len > SEG_SMALL) {
+        int q = atomicAdd(long_count, 1);
+        long_list[q] = s;
+        return;
+    }
+    // insertion sort in place (segments are short; the lines stay in L1)
+    for (int q = b + 1; q < e; ++q) {
+        int x = data[q];
+        int r = q - 1;
+        while (r >= b && data[r] > x) {
+            data[r + 1] = data[r];
+            --r;
+        }
+        data[r + 1] = x;
+    }
+}
+
+// One block per long segment: copy to scratch, then rank sort (values are
+// distinct): the element with r smaller values goes to position r.
+template <class Seg>
+__global__ void segsort_long_kernel(Seg seg, int *__restrict__ data, int *__restrict__ tmp,
+                                    const int *__restrict__ long_list,
+                                    const int *__restrict__ long_count) {
+    const int nl = *long_count;
+    for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+        int s = long_list[w];
+        int b = seg.begin(s), e = seg.end(s);
+        for (int q = b + threadIdx.x; q < e; q += blockDim.x) tmp[q] = data[q];
+        __syncthreads();
+        for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
+            int x = tmp[q];
+            int r = 0;
+            for (int u = b; u < e; ++u) r += tmp[u] < x;
+            data[b + r] = x;
+        }
+        __syncthreads();
+    }
+}
+
+struct BucketSeg {
+    const int *start;
+    __device__ int begin(int s) const { return start[s]; }
+    __device__ int end(int s) const { return start[s + 1]; }
+};
+
+struct RevSeg {   // reverse part of neighbour row s, clipped to the list capacity
+    const int *nb_start;
+    const int *own;
+    int cap;
+    __device__ int end(int s) const { return min(nb_start[s + 1], cap); }
+    __device__ int begin(int s) const { return min(nb_start[s] + own[s], end(s)); }
+};
+
+__global__ void gather_float4_kernel(const float4 *__restrict__ src, const int *__restrict__ perm,
+                                     int n, float4 *__restrict__ dst) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[perm[j]];
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int launch_scan_exclusive(const int *in, int n, int *out, int *block_sums, cudaStream_t st) {
+    int nb = (int)blocks_for((long long)n + 1, SCAN_TILE);
+    scan_reduce_kernel<<<nb, SCAN_THREADS, 0, st>>>(in, n, block_sums);
+    scan_blocks_kernel<<<1, SCAN_THREADS, 0, st>>>(block_sums, nb);
+    scan_down_kernel<<<nb, SCAN_THREADS, 0, st>>>(in, n, block_sums, out);
+    note_launch(3);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int scan_block_count(long long n) { return (int)blocks_for(n + 1, SCAN_TILE); }
+
+int launch_segsort_buckets(const int *start, int M, int *data, int *tmp, int *long_list,
+                           int *long_count, cudaStream_t st) {
+    SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
+    BucketSeg seg{start};
+    segsort_small_kernel<<<blocks_for(M, 256), 256, 0, st>>>(seg, M, data, long_list, long_count);
+    segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, long_list, long_count);
+    note_launch(2);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int *data, int *tmp,
+                        int *long_list, int *long_count, cudaStream_t st) {
+    SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
+    RevSeg seg{nb_start, own, cap};
+    segsort_small_kernel<<<blocks_for(n, 256), 256, 0, st>>>(seg, n, data, long_list, long_count);
+    segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, long_list, long_count);
+    note_launch(2);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
+                     cudaStream_t st) {
+    const unsigned init[5] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu, 0u};
+    // red is reset by a tiny kernel so the sequence stays capturable
+    grid_reset_red(red, init, st);
+    unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4 * 152);
+    if (n > 0) grid_reduce_kernel<<<nb, 256, 0, st>>>(pos_h, n, red);
+    grid_finalize_kernel<<<1, 32, 0, st>>>(red, log2_M, grid);
+    note_launch(n > 0 ? 3 : 2);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st) {
+    GridDev g{h.x0, h.y0, h.z0, h.log2_L0, h.n_levels, h.log2_M};
+    grid_set_kernel<<<1, 32, 0, st>>>(g, grid);
+    note_launch();
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_bin(const float4 *pos_h, int n, const GridDev *grid, int *key, int *count,
+               unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st) {
+    if (n > 0) {
+        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, n, grid, key, count, hmax_cell,
+                                                       lvl_count, lvl_hmax);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st) {
+    if (n > 0) {
+        scatter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key, n, start, count, perm);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st) {
+    if (n > 0) {
+        gather_float4_kernel<<<blocks_for(n, 256), 256, 0, st>>>(src, perm, n, dst);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+__global__ void reset_red_kernel(unsigned *red, unsigned a, unsigned b, unsigned c, unsigned d,
+                                 unsigned e) {
+    if (threadIdx.x == 0) {
+        red[0] = a; red[1] = b; red[2] = c; red[3] = d; red[4] = e;
+    }
+}
+
+void grid_reset_red(unsigned *red, const unsigned *v, cudaStream_t st) {
+    reset_red_kernel<<<1, 32, 0, st>>>(red, v[0], v[1], v[2], v[3], v[4]);
+}
+
+}  // namespace sphgb

@@ -1,0 +1,154 @@
+"""Density (Eq. 7) and hydrodynamic forces (Eqs. 10-11) through the C ABI
+against the FP64 oracle on the same FP32 inputs."""
+import numpy as np
+import pytest
+
+from helpers import MAX_TOL, RMS_TOL, err, need_gpu, pos_h_of
+from paper_1807_08116_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+# density is a sum of positive terms in FP32 with compensation; every term
+# carries a few roundings (1/h^3, the spline polynomial, sqrt) -> ~2e-7 each
+RHO_RMS, RHO_MAX = 1e-6, 1e-5
+
+
+def _setup(ph, cap_per=200):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    n = len(ph)
+    ctx = nv.Ctx(n, max(1024, cap_per * n))
+    x = torch.as_tensor(ph, device="cuda")
+    nv.sph_bin_and_sort(ctx, x)
+    nv.sph_build_neighbors(ctx, n)
+    return torch, nv, ctx
+
+
+def _density(ph, mass):
+    torch, nv, ctx = _setup(ph)
+    n = len(ph)
+    m = torch.as_tensor(mass, device="cuda")
+    rho = torch.empty(n, device="cuda")
+    hn = torch.empty(n, device="cuda")
+    nv.sph_density(ctx, m, rho, hn)
+    torch.cuda.synchronize()
+    return ctx, rho.cpu().numpy(), hn.cpu().numpy()
+
+
+def _forces(ph, ve, mass, rho, **params):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    n = len(ph)
+    ctx = nv.Ctx(n, max(1024, 200 * n), **params)
+    nv.sph_bin_and_sort(ctx, torch.as_tensor(ph, device="cuda"))
+    nv.sph_build_neighbors(ctx, n)
+    out = torch.full((n, 4), float("nan"), device="cuda")
+    nv.sph_forces(ctx, torch.as_tensor(ve, device="cuda"), torch.as_tensor(rho, device="cuda"),
+                  torch.as_tensor(mass, device="cuda"), out)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _gas(d):
+    ng = d["n_gas"]
+    ph = pos_h_of(d["r"][:ng], d["h"])
+    mass = d["m"][:ng].astype(np.float32)
+    ve = np.empty((ng, 4), np.float32)
+    ve[:, :3] = d["v"][:ng]
+    ve[:, 3] = d["e"]
+    return ph, mass, ve
+
+
+def _stirred(d, seed=0):
+    """Gas with a random velocity field (so viscosity and heating act) and a
+    spread of internal energies."""
+    ph, mass, ve = _gas(d)
+    rng = np.random.default_rng(seed)
+    ve[:, :3] = rng.normal(scale=0.3, size=(len(ve), 3))
+    ve[:, 3] *= rng.uniform(0.5, 1.5, len(ve))
+    return ph, mass, ve
+
+
+def test_density_single_halo(orc):
+    d = ics.single_halo(8192, 8192, seed=0)
+    ph, mass, _ = _gas(d)
+    _, rho, hn = _density(ph, mass)
+    orho, ohn = orc.density(ph, mass)
+    r1, m1 = err(rho, orho)
+    r2, m2 = err(hn, ohn)
+    print(f"density rms {r1:.2e} max {m1:.2e}; h_next rms {r2:.2e} max {m2:.2e}")
+    assert r1 <= RHO_RMS and m1 <= RHO_MAX
+    assert r2 <= RHO_RMS and m2 <= RHO_MAX
+
+
+def test_forces_single_halo(orc):
+    d = ics.single_halo(8192, 8192, seed=0)
+    ph, mass, ve = _stirred(d)
+    orho, _ = orc.density(ph, mass)
+    rho = orho.astype(np.float32)
+    a = _forces(ph, ve, mass, rho)
+    oa, ode = orc.hydro(ph, ve, mass, rho)
+    ra, ma = err(a[:, :3], oa)
+    re, me = err(a[:, 3:], ode[:, None])
+    print(f"hydro accel rms {ra:.2e} max {ma:.2e}; de/dt rms {re:.2e} max {me:.2e}")
+    assert ra <= RMS_TOL and ma <= MAX_TOL
+    assert re <= RMS_TOL and me <= MAX_TOL
+    # pairwise antisymmetry: total hydro momentum change vanishes to FP32 rounding
+    m = mass.astype(np.float64)
+    assert np.abs((m[:, None] * a[:, :3]).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(a[:, :3])).sum()
+
+
+def test_forces_at_rest_and_without_viscosity(orc):
+    d = ics.single_halo(4096, 0, seed=2)
+    ph, mass, ve = _gas(d)      # gas at rest: pressure only
+    orho, _ = orc.density(ph, mass)
+    rho = orho.astype(np.float32)
+    a = _forces(ph, ve, mass, rho, alpha=0.0, beta=0.0)
+    oa, ode = orc.hydro(ph, ve, mass, rho, alpha=0.0, beta=0.0)
+    ra, ma = err(a[:, :3], oa)
+    assert ra <= RMS_TOL and ma <= MAX_TOL
+    assert np.all(a[:, 3] == 0.0)
+
+
+def test_two_halo_sampled_rows(orc):
+    d = ics.two_halo(131072, 131072, seed=1)
+    ph, mass, ve = _stirred(d, seed=1)
+    n = len(ph)
+    rows = np.random.default_rng(5).choice(n, 300, replace=False)
+    # density on sampled rows
+    _, rho, hn = _density(ph, mass)
+    orho, ohn = orc.density(ph, mass, rows=rows)
+    r1, m1 = err(rho[rows], orho)
+    assert r1 <= RHO_RMS and m1 <= RHO_MAX
+    # forces: the common density input comes from the oracle, evaluated on the
+    # sampled rows and all their neighbours (the only densities they read)
+    ostart, oidx = orc.neighbors(ph, rows=rows)
+    need = np.unique(np.concatenate([rows, oidx]))
+    rho_need, _ = orc.density(ph, mass, rows=need)
+    rho_in = np.ones(n, np.float32)
+    rho_in[need] = rho_need.astype(np.float32)
+    a = _forces(ph, ve, mass, rho_in)
+    oa, ode = orc.hydro(ph, ve, mass, rho_in, rows=rows)
+    ra, ma = err(a[rows, :3], oa)
+    re, me = err(a[rows, 3:], ode[:, None])
+    print(f"two-halo hydro sample: accel rms {ra:.2e} max {ma:.2e}; de/dt rms {re:.2e} max {me:.2e}")
+    assert ra <= RMS_TOL and ma <= MAX_TOL
+    assert re <= RMS_TOL and me <= MAX_TOL
+
+
+def test_isolated_and_empty():
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    ph = np.array([[0, 0, 0, 0.3], [10, 0, 0, 0.3]], np.float32)
+    _, rho, hn = _density(ph, np.array([0.7, 0.7], np.float32))
+    m, h = float(np.float32(0.7)), float(np.float32(0.3))
+    assert abs(rho[0] - m / (np.pi * h ** 3)) < 1e-6 * rho[0]
+    ctx = nv.Ctx(4, 1024)
+    z = torch.zeros((0, 4), device="cuda")
+    nv.sph_bin_and_sort(ctx, z)
+    nv.sph_build_neighbors(ctx, 0)
+    e = torch.zeros(0, device="cuda")
+    nv.sph_density(ctx, e, e.clone(), e.clone())
+    nv.sph_forces(ctx, z, e, e.clone(), z.clone())
+    torch.cuda.synchronize()
