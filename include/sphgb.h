@@ -197,8 +197,14 @@ int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc
                int32_t flags, sph_stream_t stream);
 
 /* Launch plan pp_gravity uses for n particles and `flags`: *h_R targets per
- * thread (256 R per CTA) and the cluster split *h_S of the source range. */
+ * thread (256 R per CTA, R in {2, 4, 8}; pairs of targets share packed FP32x2
+ * instructions) and the cluster split *h_S of the source range. */
 int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t *h_S);
+
+/* Fix the plan of later pp_gravity calls (process-wide, for autotuning):
+ * R in {2, 4, 8}, S in {1, 2, 4, 8, 16} (clamped to the number of source
+ * tiles); R = 0 returns to the built-in cost model. */
+int sph_gravity_tune(int32_t R, int32_t S);
 
 /* Synchronise `stream`, read and clear the gravity kernel's device status
  * word (SPH_FLAG_TIMEOUT).  Returns SPH_ERR_DEVICE if a bit was set. */

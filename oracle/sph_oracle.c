@@ -17,7 +17,7 @@
  * This file must be compiled with -ffp-contract=off so that those FP32
  * expressions are evaluated one rounded operation at a time.
  *
- * Readings of the paper taken here (each one is also listed in the design doc):
+ * Readings of the paper taken here (ambiguities, garbles and silences):
  *  R1 gravity softening: Eq. 4 prints |r_i - r_j + delta|^3, which adds a
  *     scalar to a vector; read as Plummer softening (|dr|^2 + eps^2)^(3/2).
  *  R2 neighbour predicate: j is a neighbour of i (j != i) iff

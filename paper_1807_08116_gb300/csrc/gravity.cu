@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -29,7 +30,7 @@ namespace sphgb {
 
 constexpr int GR_THREADS = 256;
 constexpr int GR_TJ = 1024;                        // sources per tile
-constexpr int GR_SMEM = 2 * GR_TJ * 16 + 64;       // two tiles + two mbarriers
+constexpr int GR_SMEM = 4 * GR_TJ * 16 + 64;       // two raw tiles, one expanded, mbarriers
 
 __device__ int g_grav_flags;
 
@@ -89,13 +90,22 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
     return y;
 }
 
-template <int R, bool POT, bool GUARD, bool KAHAN>
-__global__ void __launch_bounds__(GR_THREADS)
+// Kernel: RP pairs of targets per thread (R = 2 RP).  The two targets of a
+// pair share one packed FP32x2 instruction (FADD2 / FFMA2 / FMUL2), which
+// halves the issue slots of the 12 FP32 operations of an interaction, so the
+// FP32 pipe, not instruction issue, bounds the loop.  The source tile that
+// TMA lands as (x, y, z, m) float4 is expanded once per tile into duplicated
+// pairs ((x, x, y, y), (z, z, m, m)) so each source feeds the packed operands
+// straight from two broadcast 16-byte shared loads.
+template <int RP, bool POT, bool GUARD, bool KAHAN>
+__global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : 2)
 pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, float G, float eps2,
                   float4 *__restrict__ out) {
+    constexpr int R = 2 * RP;
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *tiles = reinterpret_cast<float4 *>(smem);
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + 2 * GR_TJ * 16);
+    float4 *tiles = reinterpret_cast<float4 *>(smem);            // [2][GR_TJ] raw
+    float4 *dup = tiles + 2 * GR_TJ;                              // [GR_TJ][2] expanded
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(dup + 2 * GR_TJ);
     const int tid = threadIdx.x;
     const int rank = blockIdx.x % S;   // cluster dims (S, 1, 1): rank == ctarank
     const int i0 = (blockIdx.x / S) * (GR_THREADS * R);
@@ -103,15 +113,20 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
     const int t_end = (int)((long long)n_tiles * (rank + 1) / S);
     const int my_tiles = t_end - t_begin;
 
-    float xi[R], yi[R], zi[R];
+    // target k of this thread is i0 + tid + k * GR_THREADS; pair p = targets (2p, 2p + 1)
+    float2 nx[RP], ny[RP], nz[RP];
     Kahan ax[R], ay[R], az[R], ph[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        int i = i0 + tid + k * GR_THREADS;
-        float4 p = i < n ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        xi[k] = p.x; yi[k] = p.y; zi[k] = p.z;
-        ax[k].init(); ay[k].init(); az[k].init(); ph[k].init();
+    for (int p = 0; p < RP; ++p) {
+        int ia = i0 + tid + (2 * p) * GR_THREADS, ib = ia + GR_THREADS;
+        float4 a = ia < n ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 b = ib < n ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+        nx[p] = make_float2(-a.x, -b.x);
+        ny[p] = make_float2(-a.y, -b.y);
+        nz[p] = make_float2(-a.z, -b.z);
     }
+#pragma unroll
+    for (int k = 0; k < R; ++k) { ax[k].init(); ay[k].init(); az[k].init(); ph[k].init(); }
 
     const unsigned bar0 = smem_u32(&bars[0]);
     const unsigned tiles0 = smem_u32(tiles);
@@ -131,6 +146,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         }
     }
 
+    const float2 e2 = make_float2(eps2, eps2);
     bool failed = false;
     for (int t = 0; t < my_tiles; ++t) {
         const int buf = t & 1;
@@ -138,41 +154,12 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         if (__syncthreads_or(!ok)) { failed = true; break; }
         const int cnt = min(GR_TJ, n - (t_begin + t) * GR_TJ);
         const float4 *tb = tiles + buf * GR_TJ;
-        float sx[R], sy[R], sz[R], sp[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) { sx[k] = 0.f; sy[k] = 0.f; sz[k] = 0.f; sp[k] = 0.f; }
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j) {
-            const float4 q = tb[j];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                float dx = q.x - xi[k];
-                float dy = q.y - yi[k];
-                float dz = q.z - zi[k];
-                float r2 = fmaf(dx, dx, eps2);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                float inv = rsqrt_mufu(r2);
-                if (GUARD) inv = r2 > 0.f ? inv : 0.f;
-                float s = q.w * inv;
-                float s3 = (s * inv) * inv;
-                sx[k] = fmaf(s3, dx, sx[k]);
-                sy[k] = fmaf(s3, dy, sy[k]);
-                sz[k] = fmaf(s3, dz, sz[k]);
-                if (POT) sp[k] += s;
-            }
+        for (int q = tid; q < cnt; q += GR_THREADS) {
+            const float4 v = tb[q];
+            dup[2 * q] = make_float4(v.x, v.x, v.y, v.y);
+            dup[2 * q + 1] = make_float4(v.z, v.z, v.w, v.w);
         }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (KAHAN) {
-                ax[k].add(sx[k]); ay[k].add(sy[k]); az[k].add(sz[k]);
-                if (POT) ph[k].add(sp[k]);
-            } else {
-                ax[k].s += sx[k]; ay[k].s += sy[k]; az[k].s += sz[k];
-                if (POT) ph[k].s += sp[k];
-            }
-        }
-        __syncthreads();   // every thread is done reading this buffer
+        __syncthreads();   // raw buffer consumed, expanded tile visible
         if (tid == 0 && t + 2 < my_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             int j0 = (t_begin + t + 2) * GR_TJ;
@@ -180,6 +167,53 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
             mbar_expect_tx(bar0 + 8 * buf, bytes);
             bulk_g2s(tiles0 + buf * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * buf);
         }
+        float2 sx[RP], sy[RP], sz[RP], sp[RP];
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            sx[p] = make_float2(0.f, 0.f); sy[p] = sx[p]; sz[p] = sx[p]; sp[p] = sx[p];
+        }
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+            const float4 a = dup[2 * j];
+            const float4 b = dup[2 * j + 1];
+            const float2 qx = make_float2(a.x, a.y), qy = make_float2(a.z, a.w);
+            const float2 qz = make_float2(b.x, b.y), qm = make_float2(b.z, b.w);
+#pragma unroll
+            for (int p = 0; p < RP; ++p) {
+                const float2 dx = __fadd2_rn(qx, nx[p]);
+                const float2 dy = __fadd2_rn(qy, ny[p]);
+                const float2 dz = __fadd2_rn(qz, nz[p]);
+                float2 r2 = __ffma2_rn(dx, dx, e2);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                if (GUARD) {
+                    inv.x = r2.x > 0.f ? inv.x : 0.f;
+                    inv.y = r2.y > 0.f ? inv.y : 0.f;
+                }
+                const float2 s = __fmul2_rn(qm, inv);
+                const float2 s3 = __fmul2_rn(__fmul2_rn(s, inv), inv);
+                sx[p] = __ffma2_rn(s3, dx, sx[p]);
+                sy[p] = __ffma2_rn(s3, dy, sy[p]);
+                sz[p] = __ffma2_rn(s3, dz, sz[p]);
+                if (POT) sp[p] = __fadd2_rn(sp[p], s);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            if (KAHAN) {
+                ax[2 * p].add(sx[p].x); ax[2 * p + 1].add(sx[p].y);
+                ay[2 * p].add(sy[p].x); ay[2 * p + 1].add(sy[p].y);
+                az[2 * p].add(sz[p].x); az[2 * p + 1].add(sz[p].y);
+                if (POT) { ph[2 * p].add(sp[p].x); ph[2 * p + 1].add(sp[p].y); }
+            } else {
+                ax[2 * p].s += sx[p].x; ax[2 * p + 1].s += sx[p].y;
+                ay[2 * p].s += sy[p].x; ay[2 * p + 1].s += sy[p].y;
+                az[2 * p].s += sz[p].x; az[2 * p + 1].s += sz[p].y;
+                if (POT) { ph[2 * p].s += sp[p].x; ph[2 * p + 1].s += sp[p].y; }
+            }
+        }
+        __syncthreads();   // expanded tile fully read before the next expansion
     }
     if (failed && tid == 0) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
 
@@ -215,8 +249,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         red[3 * NB + q] = POT ? ph[k].s - ph[k].c : 0.f;
     }
     cluster.sync();
-    const int per = NB / S;
-    for (int q = rank * per + tid; q < (rank + 1) * per; q += GR_THREADS) {
+    const int q_end = NB * (rank + 1) / S;
+    for (int q = NB * rank / S + tid; q < q_end; q += GR_THREADS) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         for (int r = 0; r < S; ++r) {
             const float *peer = cluster.map_shared_rank(red, r);
@@ -241,21 +275,22 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
 
 using GravKernel = void (*)(const float4 *, int, int, int, float, float, float4 *);
 
-template <int R>
+template <int RP>
 static GravKernel pick_kernel(bool pot, bool guard, bool kahan) {
     if (pot) {
-        if (guard) return kahan ? pp_gravity_kernel<R, true, true, true> : pp_gravity_kernel<R, true, true, false>;
-        return kahan ? pp_gravity_kernel<R, true, false, true> : pp_gravity_kernel<R, true, false, false>;
+        if (guard) return kahan ? pp_gravity_kernel<RP, true, true, true> : pp_gravity_kernel<RP, true, true, false>;
+        return kahan ? pp_gravity_kernel<RP, true, false, true> : pp_gravity_kernel<RP, true, false, false>;
     }
-    if (guard) return kahan ? pp_gravity_kernel<R, false, true, true> : pp_gravity_kernel<R, false, true, false>;
-    return kahan ? pp_gravity_kernel<R, false, false, true> : pp_gravity_kernel<R, false, false, false>;
+    if (guard) return kahan ? pp_gravity_kernel<RP, false, true, true> : pp_gravity_kernel<RP, false, true, false>;
+    return kahan ? pp_gravity_kernel<RP, false, false, true> : pp_gravity_kernel<RP, false, false, false>;
 }
 
+// R targets per thread (2, 4 or 8) -> R / 2 packed pairs
 static GravKernel kernel_for(int R, bool pot, bool guard, bool kahan) {
     switch (R) {
-        case 1: return pick_kernel<1>(pot, guard, kahan);
-        case 2: return pick_kernel<2>(pot, guard, kahan);
-        default: return pick_kernel<4>(pot, guard, kahan);
+        case 2: return pick_kernel<1>(pot, guard, kahan);
+        case 8: return pick_kernel<4>(pot, guard, kahan);
+        default: return pick_kernel<2>(pot, guard, kahan);
     }
 }
 
@@ -269,8 +304,10 @@ static int slots_for(GravKernel k, int S) {
     if (S == 1) {
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, GR_THREADS, GR_SMEM) !=
-            cudaSuccess)
+            cudaSuccess) {
+            cudaGetLastError();
             return 0;
+        }
         return occ * g_num_sms;
     }
     cudaLaunchConfig_t cfg = {};
@@ -292,26 +329,37 @@ static int slots_for(GravKernel k, int S) {
     return clusters * S;
 }
 
+// Cost of a launch in "target-source pairs on the busiest SM": the grid runs
+// in waves of `slots` resident CTAs; in a wave the busiest SM holds
+// ceil(resident / SMs) CTAs, each doing 256 R x n / S interactions.
+static double plan_cost(long long units, int slots, int R, int n, int S) {
+    const double per_int = 6.0 + 1.0 + 2.0 / R;   // issue slots per interaction, packed pairs
+    const double per_cta = (double)GR_THREADS * R * ((double)n / S) * per_int;
+    long long full = units / slots, rem = units % slots;
+    double busiest = (double)full * ((slots + g_num_sms - 1) / g_num_sms) +
+                     (double)((rem + g_num_sms - 1) / g_num_sms);
+    return busiest * per_cta;
+}
+
+static std::atomic<int> g_force_R{0}, g_force_S{0};
+
 static GravPlan plan_gravity(int n, bool pot, bool guard, bool kahan) {
     const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
+    const int fR = g_force_R.load(), fS = g_force_S.load();
+    if (fR) return GravPlan{fR, std::max(1, std::min(fS, std::max(1, n_tiles)))};
     GravPlan best{4, 1};
     double best_cost = 1e300;
-    const int Rs[3] = {4, 2, 1};
+    const int Rs[3] = {4, 8, 2};
     const int Ss[5] = {1, 2, 4, 8, 16};
     for (int R : Rs) {
         GravKernel k = kernel_for(R, pot, guard, kahan);
-        const double per_int = 13.0 + 1.5 / R;   // issue slots per interaction
         const long long nib = (n + GR_THREADS * R - 1) / (GR_THREADS * R);
         for (int S : Ss) {
             if (S > 1 && S > n_tiles) break;
             int slots = slots_for(k, S);
             if (slots <= 0) continue;
-            long long units = nib * S;
-            long long waves = (units + slots - 1) / slots;
-            double resident = (double)std::min<long long>(units, slots) / g_num_sms;
-            double per_cta = (double)GR_THREADS * R * ((double)n / S) * per_int;
-            double cost = (double)waves * resident * per_cta * (1.0 + 0.002 * S);
-            if (cost < best_cost) {
+            double cost = plan_cost(nib * S, slots, R, n, S) * (1.0 + 0.01 * (S > 1) + 0.005 * S);
+            if (cost < best_cost * 0.999) {
                 best_cost = cost;
                 best = GravPlan{R, S};
             }
@@ -330,14 +378,18 @@ static void grav_init() {
         g_grav_init_status = SPH_ERR_CUDA;
         return;
     }
-    const int Rs[3] = {1, 2, 4};
+    const int Rs[3] = {2, 4, 8};
     for (int R : Rs)
         for (int f = 0; f < 8; ++f) {
             GravKernel k = kernel_for(R, f & 1, f & 2, f & 4);
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM) !=
                 cudaSuccess) {
-                cudaGetLastError();
+                g_grav_init_status = SPH_ERR_CUDA;
+                return;
             }
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess)
+                cudaGetLastError();
         }
 }
 
@@ -400,5 +452,16 @@ extern "C" int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t 
     GravPlan p = plan_gravity(n, flags & SPH_GRAV_POTENTIAL, false, !(flags & SPH_GRAV_NO_KAHAN));
     *h_R = p.R;
     *h_S = p.S;
+    return SPH_OK;
+}
+
+// Fix the launch plan of later pp_gravity calls (autotuning): R in {2, 4, 8}
+// targets per thread, S in {1, 2, 4, 8, 16} CTAs per cluster; R = 0 restores
+// the cost-model plan.
+extern "C" int sph_gravity_tune(int32_t R, int32_t S) {
+    if (R != 0 && R != 2 && R != 4 && R != 8) return SPH_ERR_INVALID_ARG;
+    if (R != 0 && S != 1 && S != 2 && S != 4 && S != 8 && S != 16) return SPH_ERR_INVALID_ARG;
+    g_force_R.store(R);
+    g_force_S.store(R ? S : 0);
     return SPH_OK;
 }

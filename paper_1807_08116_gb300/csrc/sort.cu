@@ -345,6 +345,7 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
                         int *long_list, int *long_count, cudaStream_t st) {
     SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
     RevSeg seg{nb_start, own, cap};
+    if (n == 0) return SPH_OK;
     segsort_small_kernel<<<blocks_for(n, 256), 256, 0, st>>>(seg, n, data, long_list, long_count);
     segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, long_list, long_count);
     note_launch(2);

@@ -102,6 +102,7 @@ def lib():
             "pp_gravity": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "pp_gravity_status": (_I, [_P, ctypes.POINTER(_I)]),
             "sph_gravity_plan": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+            "sph_gravity_tune": (_I, [_I, _I]),
             "integrate_step": (_I, [_I, ctypes.c_double, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                     _P, _P, _P, _P]),
             "sph_rhs_initial": (_I, [_P, ctypes.POINTER(SphState), _P]),
@@ -295,6 +296,11 @@ def sph_gravity_plan(n, flags=0):
     _check("sph_gravity_plan", lib().sph_gravity_plan(int(n), int(flags), ctypes.byref(R),
                                                       ctypes.byref(S)))
     return int(R.value), int(S.value)
+
+
+def sph_gravity_tune(R=0, S=1):
+    """Force the gravity launch plan (R targets per thread, S-CTA clusters); R=0: automatic."""
+    _check("sph_gravity_tune", lib().sph_gravity_tune(int(R), int(S)))
 
 
 def integrate_step(phase, dt, n, n_gas, r, v, e, v_save, e_save, acc_hyd, grav, mass, h,

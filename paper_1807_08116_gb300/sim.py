@@ -43,14 +43,14 @@ class Simulation:
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)
         self.ctx = None
         self.nb_per_particle = nb_per_particle
-        if ng > 0:
-            self._make_ctx(max(1024, ng * nb_per_particle))
+        # the context also carries G and eps for collisionless runs
+        self._make_ctx(max(1024, ng * nb_per_particle))
         self.diag_out = torch.zeros(8, **f64)
 
     # -- neighbour-list capacity -------------------------------------------
     def _make_ctx(self, capacity):
         old = self.ctx
-        self.ctx = nv.Ctx(self.n_gas, capacity, device=self.device, **self.params)
+        self.ctx = nv.Ctx(max(1, self.n_gas), capacity, device=self.device, **self.params)
         if old is not None:
             old.close()
 

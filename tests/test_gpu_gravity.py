@@ -117,3 +117,22 @@ def test_compensation_helps(orc):
     nk = err(_gpu_gravity(pm, flags=nv.SPH_GRAV_NO_KAHAN)[rows, :3], acc)[0]
     print(f"kahan rms {k:.2e}, plain rms {nk:.2e}")
     assert k <= nk * 1.05
+
+
+@pytest.mark.parametrize("R,S", [(2, 1), (4, 1), (8, 1), (2, 16), (4, 4), (8, 2)])
+def test_every_launch_plan(orc, R, S):
+    from paper_1807_08116_gb300 import native as nv
+    rng = np.random.default_rng(R * 100 + S)
+    n = 6001
+    pm = pos_m_of(rng.normal(size=(n, 3)), rng.uniform(0.5, 1.5, n) / n)
+    acc, pot = orc.gravity(pm)
+    need_gpu()
+    nv.sph_gravity_tune(R, S)
+    try:
+        g = _gpu_gravity(pm, flags=nv.SPH_GRAV_POTENTIAL)
+    finally:
+        nv.sph_gravity_tune(0)
+    rms, mx = err(g[:, :3], acc)
+    assert rms <= RMS_TOL and mx <= MAX_TOL, (R, S, rms, mx)
+    prms, pmx = err(g[:, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL
