@@ -28,8 +28,23 @@ namespace cg = cooperative_groups;
 
 namespace sphgb {
 
-constexpr int GR_THREADS = 256;
-constexpr int GR_TJ = 1024;                        // sources per tile
+// Launch shape (the defaults are the tuned values; the macros exist so that
+// variants can be built and timed against each other).
+#ifndef SPHGB_GR_THREADS
+#define SPHGB_GR_THREADS 256
+#endif
+#ifndef SPHGB_GR_TJ
+#define SPHGB_GR_TJ 1024
+#endif
+#ifndef SPHGB_GR_UNROLL
+#define SPHGB_GR_UNROLL 4
+#endif
+#ifndef SPHGB_GR_MINB
+#define SPHGB_GR_MINB 2
+#endif
+constexpr int GR_THREADS = SPHGB_GR_THREADS;
+constexpr int GR_UNROLL = SPHGB_GR_UNROLL;
+constexpr int GR_TJ = SPHGB_GR_TJ;                 // sources per tile
 constexpr int GR_SMEM = 4 * GR_TJ * 16 + 64;       // two raw tiles, one expanded, mbarriers
 
 __device__ int g_grav_flags;
@@ -98,7 +113,7 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 // pairs ((x, x, y, y), (z, z, m, m)) so each source feeds the packed operands
 // straight from two broadcast 16-byte shared loads.
 template <int RP, bool POT, bool GUARD, bool KAHAN>
-__global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : 2)
+__global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : SPHGB_GR_MINB)
 pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, float G, float eps2,
                   float4 *__restrict__ out) {
     constexpr int R = 2 * RP;
@@ -172,7 +187,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         for (int p = 0; p < RP; ++p) {
             sx[p] = make_float2(0.f, 0.f); sy[p] = sx[p]; sz[p] = sx[p]; sp[p] = sx[p];
         }
-#pragma unroll 4
+#pragma unroll GR_UNROLL
         for (int j = 0; j < cnt; ++j) {
             const float4 a = dup[2 * j];
             const float4 b = dup[2 * j + 1];
