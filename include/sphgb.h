@@ -132,6 +132,29 @@ int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_gas,
                      int32_t *d_cell_start_out, int32_t *d_perm_out,
                      sph_stream_t stream);
 
+/* Allocation-free variant of sph_bin_and_sort.  The paper has no counterpart:
+ * it is for callers that cannot allocate device memory -- a host framework
+ * that owns all device memory through its own fixed arena, a plugin handed
+ * only its input and output buffers, a loop that must never call cudaMalloc
+ * because it can synchronise the device.  It needs no context: its scratch is
+ * one file-scope device array of SPH_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits.  The caller passes the
+ * input d_pos_h[n_gas][4] and the results d_key[n_gas], d_cell_start[2^log2_M
+ * + 1], d_perm[n_gas] (same meaning and values as sph_bin_and_sort; no sorted
+ * copy is kept).  Limits: n_gas <= SPH_NOALLOC_MAX_GAS and log2_M <=
+ * SPH_NOALLOC_MAX_LOG2_M, else SPH_ERR_INVALID_ARG before anything runs.
+ * h_grid == NULL derives the grid on the device as sph_bin_and_sort does.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls whose
+ * work may overlap on the GPU race on it, so order them (one stream). */
+#define SPH_NOALLOC_MAX_GAS 65536
+#define SPH_NOALLOC_MAX_LOG2_M 17
+#define SPH_NOALLOC_SCRATCH_BYTES 2097152
+int sph_bin_and_sort_noalloc(const float *d_pos_h, int32_t n_gas, int32_t log2_M,
+                             const SphGrid *h_grid, int32_t *d_key, int32_t *d_cell_start,
+                             int32_t *d_perm, sph_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Neighbour lists (used by DC and HFC, Sect. 3).                            */
 /* ------------------------------------------------------------------------ */
