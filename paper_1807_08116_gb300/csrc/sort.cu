@@ -270,23 +270,96 @@ __global__ void segsort_small_kernel(Seg seg, int nseg, int *__restrict__ data,
     }
 }
 
-// One block per long segment: copy to scratch, then rank sort (values are
-// distinct): the element with r smaller values goes to position r.
+// One block per long segment.  Segments of up to SEG_CHUNK values are
+// bitonic-sorted in shared memory; longer ones are sorted chunk by chunk and
+// the sorted runs are merged pairwise, ping-ponging between the segment and
+// the same range of the scratch array, each thread producing one slice of
+// every merged run (merge path: the slice's split between the two inputs is
+// found by binary search).  Values are distinct (particle indices).
+constexpr int SEG_CHUNK = 4096;
+
+__device__ __forceinline__ void block_bitonic(int *s, int n2) {
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const int a = s[i], b = s[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ int pow2_ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Sort data[b, b + len) (len <= SEG_CHUNK) in shared memory.
+__device__ void chunk_sort(int *__restrict__ data, int b, int len, int *sm) {
+    const int n2 = pow2_ceil(len);
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) sm[q] = q < len ? data[b + q] : 0x7fffffff;
+    __syncthreads();
+    block_bitonic(sm, n2);
+    for (int q = threadIdx.x; q < len; q += blockDim.x) data[b + q] = sm[q];
+    __syncthreads();
+}
+
+// Number of elements taken from A among the first k of merge(A, B).
+__device__ __forceinline__ int co_rank(int k, const int *A, int na, const int *B, int nb) {
+    int lo = max(0, k - nb), hi = min(k, na);
+    while (lo < hi) {
+        const int i = (lo + hi) >> 1;
+        if (A[i] < B[k - i - 1]) lo = i + 1;
+        else hi = i;
+    }
+    return lo;
+}
+
 template <class Seg>
 __global__ void segsort_long_kernel(Seg seg, int *__restrict__ data, int *__restrict__ tmp,
                                     const int *__restrict__ long_list,
                                     const int *__restrict__ long_count) {
+    __shared__ int sm[SEG_CHUNK];
     const int nl = *long_count;
     for (int w = blockIdx.x; w < nl; w += gridDim.x) {
-        int s = long_list[w];
-        int b = seg.begin(s), e = seg.end(s);
-        for (int q = b + threadIdx.x; q < e; q += blockDim.x) tmp[q] = data[q];
-        __syncthreads();
-        for (int q = b + threadIdx.x; q < e; q += blockDim.x) {
-            int x = tmp[q];
-            int r = 0;
-            for (int u = b; u < e; ++u) r += tmp[u] < x;
-            data[b + r] = x;
+        const int s = long_list[w];
+        const int b = seg.begin(s), e = seg.end(s);
+        const int len = e - b;
+        if (len <= SEG_CHUNK) {
+            chunk_sort(data, b, len, sm);
+            continue;
+        }
+        for (int c0 = 0; c0 < len; c0 += SEG_CHUNK) chunk_sort(data, b + c0, min(SEG_CHUNK, len - c0), sm);
+        int *src = data, *dst = tmp;
+        for (int width = SEG_CHUNK; width < len; width *= 2) {
+            for (int p0 = 0; p0 < len; p0 += 2 * width) {
+                const int na = min(width, len - p0);
+                const int nb = max(0, min(width, len - p0 - width));
+                const int *A = src + b + p0, *B = A + na;
+                int *out = dst + b + p0;
+                const int L = na + nb;
+                const int per = (L + blockDim.x - 1) / blockDim.x;
+                const int k0 = min(L, (int)threadIdx.x * per), k1 = min(L, k0 + per);
+                int i = co_rank(k0, A, na, B, nb), j = k0 - i;
+                for (int k = k0; k < k1; ++k) {
+                    if (j >= nb || (i < na && A[i] < B[j])) out[k] = A[i++];
+                    else out[k] = B[j++];
+                }
+            }
+            __syncthreads();
+            int *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != data) {
+            for (int q = threadIdx.x; q < len; q += blockDim.x) data[b + q] = src[b + q];
         }
         __syncthreads();
     }

@@ -219,3 +219,31 @@ def test_invalid_arguments_are_rejected():
                                                    log2_M=ctx.log2_M))
     with pytest.raises(nv.SphError):
         nv.sph_build_neighbors(ctx, 7)         # no sort of 7 particles happened
+
+
+def test_giant_reverse_segments(orc):
+    # three wide particles inside 30000 narrow ones: every narrow particle
+    # reaches them from a lower level, so their rows are ~30000 long and are
+    # ordered by the chunked bitonic + merge path of the segmented sort
+    rng = np.random.default_rng(21)
+    small = pos_h_of(rng.uniform(0, 1, size=(30000, 3)), np.full(30000, 0.02))
+    big = pos_h_of(np.array([[0.5, 0.5, 0.5], [0.45, 0.5, 0.52], [0.55, 0.48, 0.5]]),
+                   np.array([0.8, 0.85, 0.9]))
+    ph = np.concatenate([small, big]).astype(np.float32)
+    n = len(ph)
+    ctx = _ctx(n, cap=n * 200)
+    ctx, key, start, perm = _sort(ph, ctx=ctx)
+    rows = np.concatenate([np.arange(30000, 30003), rng.choice(30000, 40, replace=False)])
+    start, idx, sets = _check_lists(orc, ph, ctx, perm, rows=rows)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(n, dtype=perm.dtype)
+    for i in range(30000, 30003):
+        s = inv[i]
+        row = idx[start[s]:start[s + 1]]
+        assert len(row) > 20000
+        tail = row[-20000:]          # the reverse part, canonical ascending order
+        assert np.all(np.diff(tail) > 0)
+    ctx2 = _ctx(n, cap=n * 200)
+    _sort(ph, ctx=ctx2)
+    s2, i2 = _lists(ctx2, n)
+    assert np.array_equal(s2, start) and np.array_equal(i2, idx)
