@@ -336,13 +336,162 @@ def run_e2e(sim, args, dt, barrier, dist, world, n, ng):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
 
 
+def run_ensemble(args):
+    """Batched ensemble: 64 independent two-halo collisions (total particles
+    per simulation log-uniform in [8192, 262144], impact parameter U[0, 4a],
+    speed U[0.5, 2] x escape) advanced (a) as one batch -- one launch per
+    stage, the step captured as a CUDA graph, autotuned gravity work units --
+    and (b) one simulation at a time with the single-simulation launches.
+    Prints one JSON line with both aggregate particle-steps/s and the largest
+    relative position difference between the two runs."""
+    import torch
+
+    from paper_1807_08116_gb300 import ics
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.sim import Simulation, assemble_batch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nv.lib()
+    params = ics.ensemble_params(args.n_sims, seed=3)
+    lst = [ics.from_params(**p) for p in params]
+    n_tot = sum(d["n"] for d in lst)
+    dt = 1e-3
+    ic, go, do, so = assemble_batch(lst)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # (a) batched
+    bsim = Simulation(ic, batch_offsets=(go, do, so))
+    bsim.initial_rhs()
+    tune = {}
+    pm, out = bsim.t["pos_m"], torch.empty_like(bsim.t["pos_m"])
+    for R in (2, 4, 8):
+        bsim.batch.set_plan(R)
+        nv.pp_gravity_batched(bsim.batch, pm, out)
+        tune[R] = timed(lambda: nv.pp_gravity_batched(bsim.batch, pm, out), 3) / 3
+    best_R = min(tune, key=tune.get)
+    bsim.batch.set_plan(best_R)
+    for _ in range(args.warmup):
+        bsim.step(dt)
+    bsim.capture(dt)
+    launches0 = nv.sph_launch_count()
+    ms_b = timed(lambda: bsim.replay(check=False), args.steps)
+    flags = bsim.ctx.device_status()
+    if flags:
+        raise RuntimeError(f"device flags {flags} in the batched run")
+
+    # (b) one simulation at a time
+    sims = [Simulation(d) for d in lst]
+    for sm in sims:
+        sm.initial_rhs()
+    for _ in range(args.warmup):
+        for sm in sims:
+            sm.step(dt)
+    torch.cuda.synchronize()
+
+    def seq_step():
+        for sm in sims:
+            sm.step(dt, check=False)
+    ms_s = timed(seq_step, args.steps)
+
+    rb = bsim.positions()
+    worst = 0.0
+    for k, sm in enumerate(sims):
+        r = sm.positions()
+        worst = max(worst, float(np.abs(rb[bsim.sim_slices(k)] - r).max() / max(np.abs(r).max(), 1e-30)))
+    v_b = n_tot * args.steps / (ms_b / 1e3)
+    v_s = n_tot * args.steps / (ms_s / 1e3)
+    line = {
+        "metric": "ensemble aggregate particle-steps/s", "value": v_b, "unit": "particle-steps/s",
+        "sequential_value": v_s, "speedup_vs_sequential": v_b / v_s, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
+        "sequential_ms_per_step": ms_s / args.steps, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"ensemble of {args.n_sims} two-halo collisions, "
+                               "N log-uniform in [8192, 262144], b ~ U[0,4a], v ~ U[0.5,2] v_esc",
+                   "n_total": n_tot, "n_sims": args.n_sims, "cuda_graph": True,
+                   "gravity_units_R": best_R, "autotune_ms": tune},
+        "max_rel_position_diff_batched_vs_sequential": worst,
+        "interactions_per_step": float(sum(d["n"] ** 2 for d in lst)),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving stream: Poisson arrivals (20 req/s) of two-halo jobs, sizes
+    log-uniform in [4096, 1048576], steps uniform in [10, 1000], admitted by a
+    device-memory budget (150 GB) into a continuously batched server.  The
+    offered load far exceeds one GPU, so the run is a bounded trace (the first
+    --serve-jobs arrivals) over a bounded wall-clock window; the line reports
+    offered against served load beside the latencies."""
+    import torch
+
+    from paper_1807_08116_gb300 import ics
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server, replay_trace
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nv.lib()
+    trace = ics.serving_trace(n_jobs=args.serve_jobs, rate=20.0, seed=4)
+    made = {}
+    t0 = time.perf_counter()
+    for k, req in enumerate(trace):     # inputs prepared before the clock starts
+        made[k] = ics.from_params(req["n"], req["b"], req["speed_factor"], req["seed"])
+    prep_s = time.perf_counter() - t0
+    for k, req in enumerate(trace):
+        req["k"] = k
+    server = Server(int(args.serve_budget_gb * (1 << 30)), max_resident=args.max_resident,
+                    n_streams=8)
+    jobs, steps, wall = replay_trace(server, trace, lambda req: made[req["k"]], args.serve_window)
+    done = [j for j in jobs.values() if j["state"] == nv.SIM_DONE]
+    lat = np.array([j["latency_s"] for j in done]) if done else np.zeros(0)
+    step_ms = np.array([x["ms"] for x in steps if x["resident"] or x["ms"] > 0])
+    served_ps = sum(j["steps_done"] * j["n"] for j in jobs.values())
+    served_int = sum(j["steps_done"] * float(j["n"]) ** 2 for j in jobs.values())
+    span = max(x["t"] for x in trace) - min(x["t"] for x in trace)
+    offered_ps = sum(x["steps"] * x["n"] for x in trace) / max(span, 1e-9)
+    offered_int = sum(x["steps"] * float(x["n"]) ** 2 for x in trace) / max(span, 1e-9)
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    line = {
+        "metric": "serving aggregate particle-steps/s", "value": served_ps / wall,
+        "unit": "particle-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "serving stream: Poisson 20 req/s two-halo jobs, N log-uniform "
+                               "[4096, 1048576], steps U{10..1000}",
+                   "jobs_in_trace": len(trace), "window_s": args.serve_window,
+                   "budget_gb": args.serve_budget_gb, "max_resident": args.max_resident,
+                   "input_prep_s": prep_s},
+        "step_latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "count": len(step_ms)},
+        "request_latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "completed": len(done)},
+        "offered": {"particle_steps_per_s": offered_ps, "interactions_per_s": offered_int},
+        "served": {"particle_steps_per_s": served_ps / wall, "interactions_per_s": served_int / wall},
+        "submitted": len(jobs), "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve"], default="large")
+    ap.add_argument("--n-sims", type=int, default=64)
+    ap.add_argument("--serve-jobs", type=int, default=120)
+    ap.add_argument("--serve-window", type=float, default=90.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--max-resident", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -357,6 +506,10 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

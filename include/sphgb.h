@@ -310,6 +310,117 @@ int sph_step(sph_ctx *ctx, SphState *st, double dt, sph_stream_t stream);
  * total mass, 0}. */
 int sph_diagnostics(const SphState *st, double *d_out, sph_stream_t stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent simulations advanced by the same launches.     */
+/* ------------------------------------------------------------------------ */
+
+/* A batch lays K simulations out in one SphState: all gas first, simulation
+ * by simulation (gas of s = [gas_off[s], gas_off[s+1])), then all dark
+ * (dark of s = n_gas + [dark_off[s], dark_off[s+1])), n_gas = gas_off[K].
+ * Simulations never interact: gravity sums only over a simulation's own
+ * particles, and the grid sort hashes the simulation index with the level so
+ * neighbour lists never cross simulations.  The per-simulation gravity of a
+ * batch is computed with the same tile boundaries and summation order as
+ * pp_gravity on that simulation alone with no cluster split (R and S = 1
+ * fixed by sph_gravity_tune), so it is bitwise identical to it. */
+typedef struct sph_batch sph_batch;
+
+/* Device workspace bytes of a batch (0 on invalid offsets).  h_gas_off and
+ * h_dark_off are host arrays of n_sims + 1 non-decreasing offsets from 0. */
+size_t sph_batch_workspace_bytes(int32_t n_sims, const int32_t *h_gas_off,
+                                 const int32_t *h_dark_off);
+
+/* Create a batch over caller-allocated workspace (256-byte aligned).
+ * d_sim_of_gas[n_gas] (device, caller-owned, kept by reference) gives the
+ * simulation index of every gas particle.  Uploads the per-simulation table
+ * and the gravity work list (blocks of 256 R targets, largest simulations
+ * first; R = 4) and synchronises `stream`. */
+int sph_batch_create(int32_t n_sims, const int32_t *h_gas_off, const int32_t *h_dark_off,
+                     const int32_t *d_sim_of_gas, void *d_workspace, size_t workspace_bytes,
+                     sph_stream_t stream, sph_batch **out);
+int sph_batch_destroy(sph_batch *b);
+
+/* Re-cut the gravity work list for R targets per thread (2, 4 or 8);
+ * synchronises `stream`. */
+int sph_batch_set_plan(sph_batch *b, int32_t R, sph_stream_t stream);
+
+/* Eq. 4 for every simulation of the batch in one persistent launch (work
+ * queue over the blocks of all simulations).  d_pos_m / d_acc_pot as in
+ * pp_gravity over the batch's n particles. */
+int pp_gravity_batched(const sph_batch *b, const float *d_pos_m, float G, float eps,
+                       float *d_acc_pot, int32_t flags, sph_stream_t stream);
+
+/* Attach a batch to a context (NULL detaches): later sorts use the batch's
+ * simulation map, and sph_rhs_initial / sph_step use pp_gravity_batched. */
+int sph_ctx_set_batch(sph_ctx *ctx, const sph_batch *b);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: simulations as requests (continuous batching).                   */
+/* ------------------------------------------------------------------------ */
+
+/* One simulation request: host arrays (copied by sim_submit, so the caller
+ * may free them on return): r[3n], v[3n] FP64 SoA, m[n] FP32, and for the
+ * gas particles [0, n_gas): e[n_gas] FP64 and the initial h[n_gas] FP32;
+ * n_steps predictor-corrector steps of size dt after one initial RHS. */
+typedef struct SimRequest {
+    int32_t n, n_gas, n_steps;
+    double dt;
+    const double *h_r, *h_v, *h_e;
+    const float *h_m, *h_h;
+} SimRequest;
+
+#define SIM_QUEUED  0
+#define SIM_RUNNING 1
+#define SIM_DONE    2
+#define SIM_FAILED  3
+
+/* Status of one request.  Times are seconds of a monotonic host clock.  The
+ * step latency percentiles are over the server steps the job took part in.
+ * When state == SIM_DONE, h_r / h_v / h_e point to the final state (owned by
+ * the server, valid until sim_release). */
+typedef struct SimStatus {
+    int32_t state, error, n, n_gas, n_steps, steps_done;
+    double submit_s, admit_s, done_s;
+    double step_ms_p50, step_ms_p99;
+    const double *h_r, *h_v, *h_e;
+} SimStatus;
+
+typedef struct SphServerInfo {
+    int32_t queued, resident;
+    size_t arena_bytes, arena_free_bytes;
+} SphServerInfo;
+
+typedef struct sph_server sph_server;
+
+/* A server over a caller-allocated device arena of arena_bytes (256-byte
+ * aligned): the memory budget.  Each admitted simulation takes its state
+ * and context workspace from the arena (first fit) and gives them back when
+ * it finishes.  At most max_resident simulations are advanced together, on
+ * n_streams CUDA streams the server creates. */
+int sph_server_create(const SphParams *params, void *d_arena, size_t arena_bytes,
+                      int32_t max_resident, int32_t n_streams, sph_server **out);
+int sph_server_destroy(sph_server *s);
+
+/* Queue a request (thread-safe).  SPH_ERR_BUDGET if it can never fit the
+ * arena; otherwise *job_id identifies it. */
+int sim_submit(sph_server *s, const SimRequest *req, uint64_t *job_id);
+
+/* One serving step: admit queued requests (first fit, FIFO order) while
+ * memory and slots allow, launch one step of every resident simulation (the
+ * initial RHS on its first), wait for them, retire the finished ones (final
+ * state to host, memory back to the arena).  Returns the number still
+ * resident and the wall time of the step in milliseconds (either may be
+ * NULL). */
+int sph_server_step(sph_server *s, int32_t *h_resident, double *h_step_ms);
+
+/* Status of a request (thread-safe); SPH_ERR_NOT_FOUND for an unknown id. */
+int sim_poll(sph_server *s, uint64_t job_id, SimStatus *out);
+
+/* Forget a finished, failed or still-queued request and its results. */
+int sim_release(sph_server *s, uint64_t job_id);
+
+int sph_server_info(sph_server *s, SphServerInfo *out);
+
 /* Timing helpers over the CUDA runtime (for callers without their own):
  * create / destroy `count` timing-enabled events into h_events[count], and
  * the elapsed milliseconds between two recorded events (synchronises on b). */

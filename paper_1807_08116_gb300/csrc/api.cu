@@ -2,10 +2,13 @@
 // workspace, the stage entry points SP / neighbour lists / DC / HFC, and the
 // whole-step driver that sequences them as the paper's predictor-corrector
 // flow (Sect. 2.2 and the kernel list of Sect. 3).
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <numeric>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -66,8 +69,25 @@ struct sph_ctx {
     float4 *pos_h_s, *vel_s, *aux_s;
     float *rho_s, *mass_s;
     int *own, *rev, *row_len, *nb_start, *nb_idx;
+    int *sim_s;      // simulation of each sorted particle (batched runs)
     int n_sorted;    // n_gas of the last sort
     int nb_built;    // 1 once lists match the last sort
+    int sorted_batched;        // the last sort used the batch's simulation map
+    const sph_batch *batch;    // NULL: one simulation
+};
+
+// Many independent simulations in one state (see sph_batch_create).
+struct sph_batch {
+    int n_sims, n_gas, n;
+    int R;                       // targets per thread the work units were cut for
+    std::vector<int4> h_sims;    // (g0, ng, d0, nd) per simulation
+    std::vector<int2> h_units;   // (simulation, first virtual target), largest first
+    std::vector<int> h_gas_off, h_dark_off;
+    int4 *d_sims;
+    int2 *d_units;
+    int *d_counter;
+    size_t units_cap;
+    const int *d_sim_of_gas;
 };
 
 namespace {
@@ -113,6 +133,7 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->row_len = cv.take<int>(n);
     c->nb_start = cv.take<int>(n + 1);
     c->nb_idx = cv.take<int>((size_t)c->capacity);
+    c->sim_s = cv.take<int>(n);
     *total = (cv.off + 255) & ~size_t(255);
 }
 
@@ -251,7 +272,9 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_count, 0, sizeof(int) * kMaxLevels, st));
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
     // SP1
-    if ((rc = launch_bin(pos, n_gas, ctx->grid, ctx->key, ctx->count, ctx->hmax_cell,
+    const int *sim_of = ctx->batch ? ctx->batch->d_sim_of_gas : nullptr;
+    if (sim_of && n_gas != ctx->batch->n_gas) return SPH_ERR_INVALID_ARG;
+    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->key, ctx->count, ctx->hmax_cell,
                          ctx->lvl_count, ctx->lvl_hmax, st)))
         return rc;
     // SP2 + SP3
@@ -262,6 +285,8 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
                                      ctx->long_count, st)))
         return rc;
     if ((rc = launch_gather_float4(pos, ctx->perm, n_gas, ctx->pos_h_s, st))) return rc;
+    if (sim_of && (rc = launch_gather_int(sim_of, ctx->perm, n_gas, ctx->sim_s, st))) return rc;
+    ctx->sorted_batched = sim_of != nullptr;
     ctx->n_sorted = n_gas;
     ctx->nb_built = 0;
     if (d_key_out && n_gas)
@@ -293,6 +318,7 @@ extern "C" int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_st
     a.lvl_count = ctx->lvl_count;
     a.lvl_hmax = ctx->lvl_hmax;
     a.grid = ctx->grid;
+    a.sim_s = ctx->sorted_batched ? ctx->sim_s : nullptr;
     a.n = n;
     a.own = ctx->own;
     a.rev = ctx->rev;
@@ -386,6 +412,15 @@ bool state_ok(const sph_ctx *ctx, const SphState *s) {
     return true;
 }
 
+int gravity_of(sph_ctx *ctx, SphState *s, sph_stream_t stream) {
+    const float G = ctx ? ctx->params.G : 1.0f, eps = ctx ? ctx->params.eps : 0.0f;
+    if (ctx && ctx->batch) {
+        if (ctx->batch->n != s->n || ctx->batch->n_gas != s->n_gas) return SPH_ERR_INVALID_ARG;
+        return pp_gravity_batched(ctx->batch, s->pos_m, G, eps, s->grav, s->grav_flags, stream);
+    }
+    return pp_gravity(s->pos_m, s->n, G, eps, s->grav, s->grav_flags, stream);
+}
+
 int rhs_gas(sph_ctx *ctx, SphState *s, cudaStream_t st) {
     int rc;
     if ((rc = sph_bin_and_sort(ctx, s->pos_h, s->n_gas, nullptr, nullptr, nullptr, nullptr,
@@ -407,9 +442,7 @@ extern "C" int sph_rhs_initial(sph_ctx *ctx, SphState *s, sph_stream_t stream) {
                              stream)))
         return rc;
     if (s->n_gas > 0 && (rc = rhs_gas(ctx, s, st))) return rc;
-    if ((rc = pp_gravity(s->pos_m, s->n, ctx ? ctx->params.G : 1.0f, ctx ? ctx->params.eps : 0.0f,
-                         s->grav, s->grav_flags, stream)))
-        return rc;
+    if ((rc = gravity_of(ctx, s, stream))) return rc;
     if (s->n_gas > 0 &&
         (rc = sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, stream)))
         return rc;
@@ -465,8 +498,7 @@ extern "C" int sph_step(sph_ctx *ctx, SphState *s, double dt, sph_stream_t strea
               gas ? sph_build_neighbors(ctx, s->n_gas, nullptr, nullptr, 0, nullptr, stream) : SPH_OK);
     SPH_STAGE(SPH_STAGE_DC, gas ? sph_density(ctx, s->n_gas, s->mass, s->rho, s->h, stream) : SPH_OK);
     // GFC once per step at r_{n+1}
-    SPH_STAGE(SPH_STAGE_GFC, pp_gravity(s->pos_m, s->n, ctx->params.G, ctx->params.eps, s->grav,
-                                        s->grav_flags, stream));
+    SPH_STAGE(SPH_STAGE_GFC, gravity_of(ctx, s, stream));
     // HFC at (r_{n+1}, v~, e~)
     SPH_STAGE(SPH_STAGE_HFC_CORR,
               gas ? sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, stream) : SPH_OK);
@@ -476,5 +508,143 @@ extern "C" int sph_step(sph_ctx *ctx, SphState *s, double dt, sph_stream_t strea
                              s->e_save, s->acc_hyd, s->grav, s->mass, s->h, nullptr, nullptr,
                              s->vel_e, stream));
     s->fresh = 0;
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent simulations
+// ---------------------------------------------------------------------------
+
+namespace {
+
+bool offsets_ok(int n_sims, const int32_t *off) {
+    if (!off || off[0] != 0) return false;
+    for (int s = 0; s < n_sims; ++s)
+        if (off[s + 1] < off[s]) return false;
+    return true;
+}
+
+size_t batch_units_cap(int n_sims, const int32_t *g, const int32_t *d) {
+    size_t u = 0;
+    for (int s = 0; s < n_sims; ++s) {
+        long long ns = (long long)(g[s + 1] - g[s]) + (d[s + 1] - d[s]);
+        u += (size_t)((ns + 511) / 512);   // R = 2 gives the most units
+    }
+    return u + 1;
+}
+
+struct BatchCarve {
+    size_t sims, units, counter, total;
+};
+
+BatchCarve batch_carve(int n_sims, size_t units_cap) {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    BatchCarve c;
+    c.sims = 0;
+    c.units = up(sizeof(int4) * (size_t)n_sims);
+    c.counter = c.units + up(sizeof(int2) * units_cap);
+    c.total = c.counter + 256;
+    return c;
+}
+
+int batch_build_units(sph_batch *b, int R, cudaStream_t st) {
+    const int per = 256 * R;
+    std::vector<int> order(b->n_sims);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return b->h_sims[x].y + b->h_sims[x].w > b->h_sims[y].y + b->h_sims[y].w;
+    });
+    b->h_units.clear();
+    for (int s : order) {
+        const int ns = b->h_sims[s].y + b->h_sims[s].w;
+        for (int v = 0; v < ns; v += per) b->h_units.push_back(make_int2(s, v));
+    }
+    if (b->h_units.size() > b->units_cap) return SPH_ERR_INVALID_ARG;
+    b->R = R;
+    if (!b->h_units.empty())
+        SPH_CUDA_TRY(cudaMemcpyAsync(b->d_units, b->h_units.data(), sizeof(int2) * b->h_units.size(),
+                                     cudaMemcpyHostToDevice, st));
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" size_t sph_batch_workspace_bytes(int32_t n_sims, const int32_t *h_gas_off,
+                                           const int32_t *h_dark_off) {
+    if (n_sims < 1 || !offsets_ok(n_sims, h_gas_off) || !offsets_ok(n_sims, h_dark_off)) return 0;
+    return batch_carve(n_sims, batch_units_cap(n_sims, h_gas_off, h_dark_off)).total;
+}
+
+extern "C" int sph_batch_create(int32_t n_sims, const int32_t *h_gas_off, const int32_t *h_dark_off,
+                                const int32_t *d_sim_of_gas, void *d_workspace,
+                                size_t workspace_bytes, sph_stream_t stream, sph_batch **out) {
+    if (!out || n_sims < 1 || !offsets_ok(n_sims, h_gas_off) || !offsets_ok(n_sims, h_dark_off))
+        return SPH_ERR_INVALID_ARG;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return SPH_ERR_INVALID_ARG;
+    const long long n_gas = h_gas_off[n_sims], n = n_gas + h_dark_off[n_sims];
+    if (n > 0x7fffffffLL || (n_gas > 0 && !d_sim_of_gas)) return SPH_ERR_INVALID_ARG;
+    const size_t cap = batch_units_cap(n_sims, h_gas_off, h_dark_off);
+    const BatchCarve c = batch_carve(n_sims, cap);
+    if (workspace_bytes < c.total) return SPH_ERR_INVALID_ARG;
+    sph_batch *b = new (std::nothrow) sph_batch;
+    if (!b) return SPH_ERR_INVALID_ARG;
+    b->n_sims = n_sims;
+    b->n_gas = (int)n_gas;
+    b->n = (int)n;
+    b->h_gas_off.assign(h_gas_off, h_gas_off + n_sims + 1);
+    b->h_dark_off.assign(h_dark_off, h_dark_off + n_sims + 1);
+    b->h_sims.resize(n_sims);
+    for (int s = 0; s < n_sims; ++s)
+        b->h_sims[s] = make_int4(h_gas_off[s], h_gas_off[s + 1] - h_gas_off[s],
+                                 (int)n_gas + h_dark_off[s], h_dark_off[s + 1] - h_dark_off[s]);
+    char *base = static_cast<char *>(d_workspace);
+    b->d_sims = reinterpret_cast<int4 *>(base + c.sims);
+    b->d_units = reinterpret_cast<int2 *>(base + c.units);
+    b->d_counter = reinterpret_cast<int *>(base + c.counter);
+    b->units_cap = cap;
+    b->d_sim_of_gas = d_sim_of_gas;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = SPH_OK;
+    if (cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(int4) * n_sims, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        rc = SPH_ERR_CUDA;
+    if (rc == SPH_OK) rc = batch_build_units(b, 4, st);
+    if (rc == SPH_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPH_ERR_CUDA;
+    if (rc != SPH_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SPH_OK;
+}
+
+extern "C" int sph_batch_destroy(sph_batch *b) {
+    delete b;
+    return SPH_OK;
+}
+
+extern "C" int sph_batch_set_plan(sph_batch *b, int32_t R, sph_stream_t stream) {
+    if (!b || (R != 2 && R != 4 && R != 8)) return SPH_ERR_INVALID_ARG;
+    int rc = batch_build_units(b, R, (cudaStream_t)stream);
+    if (rc) return rc;
+    SPH_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPH_OK;
+}
+
+extern "C" int pp_gravity_batched(const sph_batch *b, const float *d_pos_m, float G, float eps,
+                                  float *d_acc_pot, int32_t flags, sph_stream_t stream) {
+    if (!b || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
+    if (b->n == 0) return SPH_OK;
+    if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot))
+        return SPH_ERR_INVALID_ARG;
+    return launch_gravity_batched(reinterpret_cast<const float4 *>(d_pos_m), b->d_sims, b->d_units,
+                                  (int)b->h_units.size(), b->d_counter, b->R, G, eps,
+                                  reinterpret_cast<float4 *>(d_acc_pot), flags, (cudaStream_t)stream);
+}
+
+extern "C" int sph_ctx_set_batch(sph_ctx *ctx, const sph_batch *b) {
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (b && b->n_gas > ctx->n_max) return SPH_ERR_INVALID_ARG;
+    ctx->batch = b;
     return SPH_OK;
 }

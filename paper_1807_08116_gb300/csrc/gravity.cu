@@ -20,7 +20,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -105,6 +107,79 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
     return y;
 }
 
+// Expand a landed tile (x, y, z, m) into duplicated pairs ((x, x, y, y),
+// (z, z, m, m)), one per source.
+__device__ __forceinline__ void expand_tile(const float4 *__restrict__ tb, float4 *__restrict__ dup,
+                                            int cnt) {
+    for (int q = threadIdx.x; q < cnt; q += GR_THREADS) {
+        const float4 v = tb[q];
+        dup[2 * q] = make_float4(v.x, v.x, v.y, v.y);
+        dup[2 * q + 1] = make_float4(v.z, v.z, v.w, v.w);
+    }
+}
+
+// Sums of one tile for RP target pairs: 3 FADD2, 3 FFMA2, 2 MUFU.RSQ,
+// 3 FMUL2, 3 FFMA2 (+1 FADD2 for the potential) per source and pair.
+template <int RP, bool POT, bool GUARD>
+__device__ __forceinline__ void tile_sums(const float4 *__restrict__ dup, int cnt,
+                                          const float2 (&nx)[RP], const float2 (&ny)[RP],
+                                          const float2 (&nz)[RP], float2 e2, float2 (&sx)[RP],
+                                          float2 (&sy)[RP], float2 (&sz)[RP], float2 (&sp)[RP]) {
+#pragma unroll
+    for (int p = 0; p < RP; ++p) {
+        sx[p] = make_float2(0.f, 0.f); sy[p] = sx[p]; sz[p] = sx[p]; sp[p] = sx[p];
+    }
+#pragma unroll GR_UNROLL
+    for (int j = 0; j < cnt; ++j) {
+        const float4 a = dup[2 * j];
+        const float4 b = dup[2 * j + 1];
+        const float2 qx = make_float2(a.x, a.y), qy = make_float2(a.z, a.w);
+        const float2 qz = make_float2(b.x, b.y), qm = make_float2(b.z, b.w);
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            const float2 dx = __fadd2_rn(qx, nx[p]);
+            const float2 dy = __fadd2_rn(qy, ny[p]);
+            const float2 dz = __fadd2_rn(qz, nz[p]);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+            if (GUARD) {
+                inv.x = r2.x > 0.f ? inv.x : 0.f;
+                inv.y = r2.y > 0.f ? inv.y : 0.f;
+            }
+            const float2 s = __fmul2_rn(qm, inv);
+            const float2 s3 = __fmul2_rn(__fmul2_rn(s, inv), inv);
+            sx[p] = __ffma2_rn(s3, dx, sx[p]);
+            sy[p] = __ffma2_rn(s3, dy, sy[p]);
+            sz[p] = __ffma2_rn(s3, dz, sz[p]);
+            if (POT) sp[p] = __fadd2_rn(sp[p], s);
+        }
+    }
+}
+
+// Fold one tile's partial sums into the running (compensated) sums.
+template <int RP, bool POT, bool KAHAN>
+__device__ __forceinline__ void fold_tile(Kahan (&ax)[2 * RP], Kahan (&ay)[2 * RP],
+                                          Kahan (&az)[2 * RP], Kahan (&ph)[2 * RP],
+                                          const float2 (&sx)[RP], const float2 (&sy)[RP],
+                                          const float2 (&sz)[RP], const float2 (&sp)[RP]) {
+#pragma unroll
+    for (int p = 0; p < RP; ++p) {
+        if (KAHAN) {
+            ax[2 * p].add(sx[p].x); ax[2 * p + 1].add(sx[p].y);
+            ay[2 * p].add(sy[p].x); ay[2 * p + 1].add(sy[p].y);
+            az[2 * p].add(sz[p].x); az[2 * p + 1].add(sz[p].y);
+            if (POT) { ph[2 * p].add(sp[p].x); ph[2 * p + 1].add(sp[p].y); }
+        } else {
+            ax[2 * p].s += sx[p].x; ax[2 * p + 1].s += sx[p].y;
+            ay[2 * p].s += sy[p].x; ay[2 * p + 1].s += sy[p].y;
+            az[2 * p].s += sz[p].x; az[2 * p + 1].s += sz[p].y;
+            if (POT) { ph[2 * p].s += sp[p].x; ph[2 * p + 1].s += sp[p].y; }
+        }
+    }
+}
+
 // Kernel: RP pairs of targets per thread (R = 2 RP).  The two targets of a
 // pair share one packed FP32x2 instruction (FADD2 / FFMA2 / FMUL2), which
 // halves the issue slots of the 12 FP32 operations of an interaction, so the
@@ -169,11 +244,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         if (__syncthreads_or(!ok)) { failed = true; break; }
         const int cnt = min(GR_TJ, n - (t_begin + t) * GR_TJ);
         const float4 *tb = tiles + buf * GR_TJ;
-        for (int q = tid; q < cnt; q += GR_THREADS) {
-            const float4 v = tb[q];
-            dup[2 * q] = make_float4(v.x, v.x, v.y, v.y);
-            dup[2 * q + 1] = make_float4(v.z, v.z, v.w, v.w);
-        }
+        expand_tile(tb, dup, cnt);
         __syncthreads();   // raw buffer consumed, expanded tile visible
         if (tid == 0 && t + 2 < my_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -183,51 +254,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
             bulk_g2s(tiles0 + buf * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * buf);
         }
         float2 sx[RP], sy[RP], sz[RP], sp[RP];
-#pragma unroll
-        for (int p = 0; p < RP; ++p) {
-            sx[p] = make_float2(0.f, 0.f); sy[p] = sx[p]; sz[p] = sx[p]; sp[p] = sx[p];
-        }
-#pragma unroll GR_UNROLL
-        for (int j = 0; j < cnt; ++j) {
-            const float4 a = dup[2 * j];
-            const float4 b = dup[2 * j + 1];
-            const float2 qx = make_float2(a.x, a.y), qy = make_float2(a.z, a.w);
-            const float2 qz = make_float2(b.x, b.y), qm = make_float2(b.z, b.w);
-#pragma unroll
-            for (int p = 0; p < RP; ++p) {
-                const float2 dx = __fadd2_rn(qx, nx[p]);
-                const float2 dy = __fadd2_rn(qy, ny[p]);
-                const float2 dz = __fadd2_rn(qz, nz[p]);
-                float2 r2 = __ffma2_rn(dx, dx, e2);
-                r2 = __ffma2_rn(dy, dy, r2);
-                r2 = __ffma2_rn(dz, dz, r2);
-                float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-                if (GUARD) {
-                    inv.x = r2.x > 0.f ? inv.x : 0.f;
-                    inv.y = r2.y > 0.f ? inv.y : 0.f;
-                }
-                const float2 s = __fmul2_rn(qm, inv);
-                const float2 s3 = __fmul2_rn(__fmul2_rn(s, inv), inv);
-                sx[p] = __ffma2_rn(s3, dx, sx[p]);
-                sy[p] = __ffma2_rn(s3, dy, sy[p]);
-                sz[p] = __ffma2_rn(s3, dz, sz[p]);
-                if (POT) sp[p] = __fadd2_rn(sp[p], s);
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < RP; ++p) {
-            if (KAHAN) {
-                ax[2 * p].add(sx[p].x); ax[2 * p + 1].add(sx[p].y);
-                ay[2 * p].add(sy[p].x); ay[2 * p + 1].add(sy[p].y);
-                az[2 * p].add(sz[p].x); az[2 * p + 1].add(sz[p].y);
-                if (POT) { ph[2 * p].add(sp[p].x); ph[2 * p + 1].add(sp[p].y); }
-            } else {
-                ax[2 * p].s += sx[p].x; ax[2 * p + 1].s += sx[p].y;
-                ay[2 * p].s += sy[p].x; ay[2 * p + 1].s += sy[p].y;
-                az[2 * p].s += sz[p].x; az[2 * p + 1].s += sz[p].y;
-                if (POT) { ph[2 * p].s += sp[p].x; ph[2 * p + 1].s += sp[p].y; }
-            }
-        }
+        tile_sums<RP, POT, GUARD>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp);
+        fold_tile<RP, POT, KAHAN>(ax, ay, az, ph, sx, sy, sz, sp);
         __syncthreads();   // expanded tile fully read before the next expansion
     }
     if (failed && tid == 0) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
@@ -281,6 +309,116 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
         }
     }
     cluster.sync();
+}
+
+// Batched form: many independent simulations in one persistent launch.
+// Simulation s owns gas particles [g0, g0 + ng) and dark particles
+// [d0, d0 + nd) of the shared arrays; its particles are numbered "virtually"
+// v = 0..ng+nd-1 (gas first), exactly the order a single-simulation launch
+// of that simulation sees, so its sums (tile boundaries, summation order) are
+// the same as pp_gravity's with no cluster split.  A work unit is (s, first
+// virtual target of a block of 256 R); units are taken from a queue
+// (atomic counter) in decreasing order of simulation size, so the largest
+// blocks start first.  A tile that straddles the gas/dark boundary is landed
+// with two bulk copies on one mbarrier.
+template <int RP, bool POT, bool GUARD, bool KAHAN>
+__global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : SPHGB_GR_MINB)
+pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict__ sims,
+                          const int2 *__restrict__ units, int n_units, int *__restrict__ counter,
+                          float G, float eps2, float4 *__restrict__ out) {
+    constexpr int R = 2 * RP;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_unit;
+    float4 *tiles = reinterpret_cast<float4 *>(smem);
+    float4 *dup = tiles + 2 * GR_TJ;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(dup + 2 * GR_TJ);
+    const int tid = threadIdx.x;
+    const unsigned bar0 = smem_u32(&bars[0]);
+    const unsigned tiles0 = smem_u32(tiles);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    const float2 e2 = make_float2(eps2, eps2);
+    const float self_inv = GUARD ? 0.f : rsqrt_mufu(eps2);
+    unsigned seq = 0;   // tiles this CTA has landed so far (mbarrier phases)
+    bool failed = false;
+    for (;;) {
+        if (tid == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= n_units || failed) break;
+        const int2 un = units[u];
+        const int4 sr = sims[un.x];   // (g0, ng, d0, nd)
+        const int ng = sr.y, ns = sr.y + sr.w;
+        const int vt0 = un.y;
+        const int nt = (ns + GR_TJ - 1) / GR_TJ;
+
+        float2 nx[RP], ny[RP], nz[RP];
+        Kahan ax[R], ay[R], az[R], ph[R];
+#pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            const int va = vt0 + tid + (2 * p) * GR_THREADS, vb = va + GR_THREADS;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (va < ns) a = pos[va < ng ? sr.x + va : sr.z + (va - ng)];
+            if (vb < ns) b = pos[vb < ng ? sr.x + vb : sr.z + (vb - ng)];
+            nx[p] = make_float2(-a.x, -b.x);
+            ny[p] = make_float2(-a.y, -b.y);
+            nz[p] = make_float2(-a.z, -b.z);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) { ax[k].init(); ay[k].init(); az[k].init(); ph[k].init(); }
+
+        // land virtual source tile t into buffer (seq + t) & 1
+        auto issue = [&](int t) {
+            const int v0 = t * GR_TJ, v1 = min(ns, v0 + GR_TJ);
+            const int gcnt = max(0, min(v1, ng) - v0);
+            const int dcnt = (v1 - v0) - gcnt;
+            const unsigned buf = (seq + t) & 1u;
+            const unsigned bar = bar0 + 8 * buf, dst = tiles0 + buf * GR_TJ * 16;
+            mbar_expect_tx(bar, (unsigned)(v1 - v0) * 16u);
+            if (gcnt) bulk_g2s(dst, pos + sr.x + v0, (unsigned)gcnt * 16u, bar);
+            if (dcnt) bulk_g2s(dst + gcnt * 16, pos + sr.z + max(0, v0 - ng), (unsigned)dcnt * 16u, bar);
+        };
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int b = 0; b < 2 && b < nt; ++b) issue(b);
+        }
+        for (int t = 0; t < nt; ++t) {
+            const unsigned q = seq + t;
+            const int buf = q & 1;
+            bool ok = mbar_wait_bounded(bar0 + 8 * buf, (q >> 1) & 1u);
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            const int cnt = min(GR_TJ, ns - t * GR_TJ);
+            expand_tile(tiles + buf * GR_TJ, dup, cnt);
+            __syncthreads();
+            if (tid == 0 && t + 2 < nt) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(t + 2);
+            }
+            float2 sx[RP], sy[RP], sz[RP], sp[RP];
+            tile_sums<RP, POT, GUARD>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp);
+            fold_tile<RP, POT, KAHAN>(ax, ay, az, ph, sx, sy, sz, sp);
+            __syncthreads();
+        }
+        seq += nt;
+        if (failed) break;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int v = vt0 + tid + k * GR_THREADS;
+            if (v < ns) {
+                const int i = v < ng ? sr.x + v : sr.z + (v - ng);
+                const float m_i = pos[i].w;
+                const float pot = POT ? -G * ((ph[k].s - ph[k].c) - m_i * self_inv) : 0.f;
+                out[i] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
+                                     G * (az[k].s - az[k].c), pot);
+            }
+        }
+    }
+    if (failed && tid == 0) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,10 +496,30 @@ static double plan_cost(long long units, int slots, int R, int n, int S) {
 
 static std::atomic<int> g_force_R{0}, g_force_S{0};
 
+static GravPlan plan_gravity_uncached(int n, bool pot, bool guard, bool kahan);
+
+// Plans are cached per (n, variant) so that repeated launches (and launches
+// recorded into a CUDA graph) make no occupancy queries.
+static std::mutex g_plan_mutex;
+static std::map<std::tuple<int, int>, GravPlan> g_plan_cache;
+
 static GravPlan plan_gravity(int n, bool pot, bool guard, bool kahan) {
-    const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
     const int fR = g_force_R.load(), fS = g_force_S.load();
-    if (fR) return GravPlan{fR, std::max(1, std::min(fS, std::max(1, n_tiles)))};
+    if (fR) {
+        const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
+        return GravPlan{fR, std::max(1, std::min(fS, std::max(1, n_tiles)))};
+    }
+    const auto key = std::make_tuple(n, (pot ? 1 : 0) | (guard ? 2 : 0) | (kahan ? 4 : 0));
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    auto it = g_plan_cache.find(key);
+    if (it != g_plan_cache.end()) return it->second;
+    GravPlan p = plan_gravity_uncached(n, pot, guard, kahan);
+    g_plan_cache[key] = p;
+    return p;
+}
+
+static GravPlan plan_gravity_uncached(int n, bool pot, bool guard, bool kahan) {
+    const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
     GravPlan best{4, 1};
     double best_cost = 1e300;
     const int Rs[3] = {4, 8, 2};
@@ -406,6 +564,81 @@ static void grav_init() {
                 cudaSuccess)
                 cudaGetLastError();
         }
+}
+
+using GravBatchedKernel = void (*)(const float4 *, const int4 *, const int2 *, int, int *, float,
+                                   float, float4 *);
+
+template <int RP>
+static GravBatchedKernel pick_batched(bool pot, bool guard, bool kahan) {
+    if (pot) {
+        if (guard) return kahan ? pp_gravity_batched_kernel<RP, true, true, true> : pp_gravity_batched_kernel<RP, true, true, false>;
+        return kahan ? pp_gravity_batched_kernel<RP, true, false, true> : pp_gravity_batched_kernel<RP, true, false, false>;
+    }
+    if (guard) return kahan ? pp_gravity_batched_kernel<RP, false, true, true> : pp_gravity_batched_kernel<RP, false, true, false>;
+    return kahan ? pp_gravity_batched_kernel<RP, false, false, true> : pp_gravity_batched_kernel<RP, false, false, false>;
+}
+
+static GravBatchedKernel batched_for(int R, bool pot, bool guard, bool kahan) {
+    switch (R) {
+        case 2: return pick_batched<1>(pot, guard, kahan);
+        case 8: return pick_batched<4>(pot, guard, kahan);
+        default: return pick_batched<2>(pot, guard, kahan);
+    }
+}
+
+static std::once_flag g_grav_batched_once;
+static int g_grav_batched_status = SPH_OK;
+
+static void grav_batched_init() {
+    const int Rs[3] = {2, 4, 8};
+    for (int R : Rs)
+        for (int f = 0; f < 8; ++f)
+            if (cudaFuncSetAttribute(batched_for(R, f & 1, f & 2, f & 4),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     GR_SMEM) != cudaSuccess) {
+                g_grav_batched_status = SPH_ERR_CUDA;
+                return;
+            }
+}
+
+int gravity_num_sms() {
+    std::call_once(g_grav_once, grav_init);
+    return g_num_sms;
+}
+
+int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *units, int n_units,
+                           int *counter, int R, float G, float eps, float4 *out, int flags,
+                           cudaStream_t st) {
+    std::call_once(g_grav_once, grav_init);
+    if (g_grav_init_status != SPH_OK) return g_grav_init_status;
+    std::call_once(g_grav_batched_once, grav_batched_init);
+    if (g_grav_batched_status != SPH_OK) return g_grav_batched_status;
+    if (n_units <= 0) return SPH_OK;
+    const bool pot = flags & SPH_GRAV_POTENTIAL;
+    const bool kahan = !(flags & SPH_GRAV_NO_KAHAN);
+    const float eps2 = eps * eps;
+    const bool guard = !(eps2 > 0.0f);
+    GravBatchedKernel k = batched_for(R, pot, guard, kahan);
+    static std::mutex occ_mutex;
+    static std::map<GravBatchedKernel, int> occ_cache;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(occ_mutex);
+        auto it = occ_cache.find(k);
+        if (it != occ_cache.end()) {
+            occ = it->second;
+        } else {
+            SPH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, GR_THREADS, GR_SMEM));
+            occ_cache[k] = occ;
+        }
+    }
+    const int grid = std::max(1, std::min(n_units, occ * g_num_sms));
+    SPH_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    k<<<grid, GR_THREADS, GR_SMEM, st>>>(pos, sims, units, n_units, counter, G, eps2, out);
+    note_launch();
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
 }
 
 }  // namespace sphgb

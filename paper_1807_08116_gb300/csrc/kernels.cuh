@@ -15,11 +15,19 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
 int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
                      cudaStream_t st);
 int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st);
-int launch_bin(const float4 *pos_h, int n, const GridDev *grid, int *key, int *count,
-               unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st);
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
+               int *count, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
+               cudaStream_t st);
+int launch_gather_int(const int *src, const int *perm, int n, int *dst, cudaStream_t st);
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
 int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st);
 void grid_reset_red(unsigned *red, const unsigned *v, cudaStream_t st);
+
+// gravity.cu: the batched kernel's work description (host side)
+int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *units, int n_units,
+                           int *counter, int R, float G, float eps, float4 *out, int flags,
+                           cudaStream_t st);
+int gravity_num_sms();
 
 // neighbors.cu
 struct NbArgs {
@@ -29,6 +37,7 @@ struct NbArgs {
     const int *lvl_count;    // [kMaxLevels]
     const unsigned *lvl_hmax;
     const GridDev *grid;
+    const int *sim_s;        // [n] simulation of each sorted particle, or NULL (one simulation)
     int n;
     int *own;                // [n] own-search count
     int *rev;                // [n] reverse count / cursor

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
     const GridDev g = *a.grid;
     const float4 p = a.pos_h_s[i];
     const int li = level_of(p.w, g.log2_L0, g.n_levels);
+    const int si = a.sim_s ? a.sim_s[i] : 0;
     int cnt = 0;
     long long base = 0;
     if (FILL) base = a.nb_start[i];
@@ -59,10 +60,11 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
         for (int cz = lz; cz <= hz; ++cz)
             for (int cy = ly; cy <= hy; ++cy)
                 for (int cx = lx; cx <= hx; ++cx) {
-                    const int k = bucket_of(cx, cy, cz, l, g.log2_M);
+                    const int k = bucket_of(cx, cy, cz, l + kMaxLevels * si, g.log2_M);
                     const int s = a.cell_start[k], e = a.cell_start[k + 1];
                     for (int j = s; j < e; ++j) {
                         if (j == i) continue;
+                        if (a.sim_s && a.sim_s[j] != si) continue;
                         const float4 q = a.pos_h_s[j];
                         if (level_of(q.w, g.log2_L0, g.n_levels) != l) continue;
                         if (cell_of(q.x, g.x0, inv_c) != cx || cell_of(q.y, g.y0, inv_c) != cy ||

@@ -103,8 +103,9 @@ __global__ void grid_set_kernel(GridDev g, GridDev *grid) {
 // count and max h.
 // ---------------------------------------------------------------------------
 
-__global__ void bin_kernel(const float4 *__restrict__ pos_h, int n, const GridDev *__restrict__ gridp,
-                           int *__restrict__ key, int *__restrict__ count,
+__global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restrict__ sim_of, int n,
+                           const GridDev *__restrict__ gridp, int *__restrict__ key,
+                           int *__restrict__ count,
                            unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
                            unsigned *__restrict__ lvl_hmax) {
     __shared__ int s_cnt[kMaxLevels];
@@ -123,7 +124,10 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, int n, const GridDe
         int cx = cell_of(p.x, g.x0, inv_c);
         int cy = cell_of(p.y, g.y0, inv_c);
         int cz = cell_of(p.z, g.z0, inv_c);
-        int k = bucket_of(cx, cy, cz, l, g.log2_M);
+        // simulations of a batch share the grid; the simulation index enters
+        // the bucket hash next to the level (0 for a single simulation)
+        const int sim = sim_of ? sim_of[i] : 0;
+        int k = bucket_of(cx, cy, cz, l + kMaxLevels * sim, g.log2_M);
         key[i] = k;
         atomicAdd(&count[k], 1);
         unsigned hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
@@ -379,6 +383,12 @@ struct RevSeg {   // reverse part of neighbour row s, clipped to the list capaci
     __device__ int begin(int s) const { return min(nb_start[s] + own[s], end(s)); }
 };
 
+__global__ void gather_int_kernel(const int *__restrict__ src, const int *__restrict__ perm, int n,
+                                  int *__restrict__ dst) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) dst[j] = src[perm[j]];
+}
+
 __global__ void gather_float4_kernel(const float4 *__restrict__ src, const int *__restrict__ perm,
                                      int n, float4 *__restrict__ dst) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -447,10 +457,11 @@ int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st) {
     return SPH_OK;
 }
 
-int launch_bin(const float4 *pos_h, int n, const GridDev *grid, int *key, int *count,
-               unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st) {
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
+               int *count, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
+               cudaStream_t st) {
     if (n > 0) {
-        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, n, grid, key, count, hmax_cell,
+        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, n, grid, key, count, hmax_cell,
                                                        lvl_count, lvl_hmax);
         note_launch();
     }
@@ -461,6 +472,15 @@ int launch_bin(const float4 *pos_h, int n, const GridDev *grid, int *key, int *c
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st) {
     if (n > 0) {
         scatter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key, n, start, count, perm);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_gather_int(const int *src, const int *perm, int n, int *dst, cudaStream_t st) {
+    if (n > 0) {
+        gather_int_kernel<<<blocks_for(n, 256), 256, 0, st>>>(src, perm, n, dst);
         note_launch();
     }
     SPH_LAUNCH_CHECK();

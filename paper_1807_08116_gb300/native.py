@@ -62,6 +62,27 @@ class SphState(ctypes.Structure):
                                        "pos_h", "vel_e", "rho", "acc_hyd", "grav")] + [
         ("fresh", ctypes.c_int32), ("grav_flags", ctypes.c_int32), ("events", ctypes.c_void_p)]
 
+class SimRequest(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_gas", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("dt", ctypes.c_double)] + [(k, ctypes.c_void_p) for k in
+                                            ("h_r", "h_v", "h_e", "h_m", "h_h")]
+
+
+class SimStatus(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("state", "error", "n", "n_gas", "n_steps",
+                                              "steps_done")] + [
+        (k, ctypes.c_double) for k in ("submit_s", "admit_s", "done_s", "step_ms_p50",
+                                       "step_ms_p99")] + [
+        (k, ctypes.c_void_p) for k in ("h_r", "h_v", "h_e")]
+
+
+class SphServerInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("resident", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_size_t), ("arena_free_bytes", ctypes.c_size_t)]
+
+
+SIM_QUEUED, SIM_RUNNING, SIM_DONE, SIM_FAILED = 0, 1, 2, 3
+
 STAGES = ("hfc_pred", "su_pred", "sp", "nb", "dc", "gfc", "hfc_corr", "su_corr")
 
 
@@ -112,6 +133,20 @@ def lib():
             "sph_events_destroy": (_I, [_I, _P]),
             "sph_event_elapsed_ms": (_I, [_P, _P, ctypes.POINTER(ctypes.c_float)]),
             "sph_launch_count": (ctypes.c_int64, []),
+            "sph_batch_workspace_bytes": (ctypes.c_size_t, [_I, _P, _P]),
+            "sph_batch_create": (_I, [_I, _P, _P, _P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+            "sph_batch_destroy": (_I, [_P]),
+            "sph_batch_set_plan": (_I, [_P, _I, _P]),
+            "pp_gravity_batched": (_I, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
+            "sph_ctx_set_batch": (_I, [_P, _P]),
+            "sph_server_create": (_I, [ctypes.POINTER(SphParams), _P, ctypes.c_size_t, _I, _I,
+                                       ctypes.POINTER(_P)]),
+            "sph_server_destroy": (_I, [_P]),
+            "sim_submit": (_I, [_P, ctypes.POINTER(SimRequest), ctypes.POINTER(ctypes.c_uint64)]),
+            "sph_server_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+            "sim_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(SimStatus)]),
+            "sim_release": (_I, [_P, ctypes.c_uint64]),
+            "sph_server_info": (_I, [_P, ctypes.POINTER(SphServerInfo)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -382,3 +417,60 @@ def sph_diagnostics(state: SphState, out, stream=None):
     _check("sph_diagnostics", lib().sph_diagnostics(ctypes.byref(state),
                                                     _ptr(out, torch.float64, (8,), "out"),
                                                     _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Batches of independent simulations
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """A batch descriptor: per-simulation gas / dark offsets (host) and the
+    simulation index of every gas particle (device), plus its workspace."""
+
+    def __init__(self, gas_off, dark_off, sim_of_gas, stream=None):
+        import numpy as np
+        self.gas_off = np.ascontiguousarray(gas_off, np.int32)
+        self.dark_off = np.ascontiguousarray(dark_off, np.int32)
+        self.n_sims = len(self.gas_off) - 1
+        self.sim_of_gas = sim_of_gas
+        gp = self.gas_off.ctypes.data_as(ctypes.c_void_p)
+        dp = self.dark_off.ctypes.data_as(ctypes.c_void_p)
+        nbytes = int(lib().sph_batch_workspace_bytes(self.n_sims, gp, dp))
+        if nbytes == 0:
+            raise SphError("sph_batch_workspace_bytes", SPH_ERR_INVALID_ARG)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=sim_of_gas.device)
+        ptr = self.workspace.data_ptr() + ((-self.workspace.data_ptr()) % 256)
+        h = ctypes.c_void_p()
+        n_gas = int(self.gas_off[-1])
+        rc = lib().sph_batch_create(self.n_sims, gp, dp,
+                                    _ptr(sim_of_gas, torch.int32, (n_gas,), "sim_of_gas", n_gas == 0),
+                                    ctypes.c_void_p(ptr), nbytes, _stream(stream), ctypes.byref(h))
+        _check("sph_batch_create", rc)
+        self.handle = h
+
+    def set_plan(self, R, stream=None):
+        _check("sph_batch_set_plan", lib().sph_batch_set_plan(self.handle, int(R), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().sph_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pp_gravity_batched(batch, pos_m, acc_pot, G=1.0, eps=0.01, flags=0, stream=None):
+    n = pos_m.shape[0]
+    rc = lib().pp_gravity_batched(batch.handle, _ptr(pos_m, torch.float32, (n, 4), "pos_m"),
+                                  float(G), float(eps),
+                                  _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"), int(flags),
+                                  _stream(stream))
+    _check("pp_gravity_batched", rc)
+
+
+def sph_ctx_set_batch(ctx, batch):
+    _check("sph_ctx_set_batch", lib().sph_ctx_set_batch(ctx.handle, batch.handle if batch else None))

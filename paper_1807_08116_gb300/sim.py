@@ -13,8 +13,35 @@ import torch
 from . import native as nv
 
 
+def assemble_batch(ic_list):
+    """Lay several initial conditions out as one batched state: all gas
+    (simulation by simulation), then all dark.  Returns (ic, gas_off,
+    dark_off, sim_of_gas)."""
+    gas_off = [0]
+    dark_off = [0]
+    rg, vg, rd, vd, e, h, mg, md, sim = [], [], [], [], [], [], [], [], []
+    for s, d in enumerate(ic_list):
+        ng = int(d["n_gas"])
+        rg.append(d["r"][:ng]); vg.append(d["v"][:ng])
+        rd.append(d["r"][ng:]); vd.append(d["v"][ng:])
+        e.append(d["e"]); h.append(d["h"])
+        mg.append(d["m"][:ng]); md.append(d["m"][ng:])
+        sim.append(np.full(ng, s, np.int32))
+        gas_off.append(gas_off[-1] + ng)
+        dark_off.append(dark_off[-1] + int(d["n"]) - ng)
+    r = np.concatenate(rg + rd)
+    out = dict(r=r, v=np.concatenate(vg + vd), e=np.concatenate(e), h=np.concatenate(h),
+               m=np.concatenate(mg + md), n_gas=gas_off[-1], n=r.shape[0])
+    return out, np.array(gas_off, np.int32), np.array(dark_off, np.int32), np.concatenate(sim)
+
+
 class Simulation:
-    def __init__(self, ic: dict, device=None, grav_flags=0, nb_per_particle=120, **params):
+    """One simulation, or a batch of independent ones (batch_offsets =
+    (gas_off, dark_off, sim_of_gas) from assemble_batch), resident in device
+    memory and advanced by sph_step."""
+
+    def __init__(self, ic: dict, device=None, grav_flags=0, nb_per_particle=120,
+                 batch_offsets=None, **params):
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self.params = dict(nv.DEFAULT_PARAMS)
@@ -43,16 +70,26 @@ class Simulation:
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)
         self.ctx = None
         self.nb_per_particle = nb_per_particle
+        self.batch = None
+        if batch_offsets is not None:
+            gas_off, dark_off, sim_of_gas = batch_offsets
+            self.sim_of_gas = torch.as_tensor(np.asarray(sim_of_gas, np.int32), device=dev)
+            self.batch = nv.Batch(gas_off, dark_off, self.sim_of_gas)
+            self.gas_off, self.dark_off = np.asarray(gas_off), np.asarray(dark_off)
         # the context also carries G and eps for collisionless runs
         self._make_ctx(max(1024, ng * nb_per_particle))
+        self.graph = None
         self.diag_out = torch.zeros(8, **f64)
 
     # -- neighbour-list capacity -------------------------------------------
     def _make_ctx(self, capacity):
         old = self.ctx
         self.ctx = nv.Ctx(max(1, self.n_gas), capacity, device=self.device, **self.params)
+        if self.batch is not None:
+            nv.sph_ctx_set_batch(self.ctx, self.batch)
         if old is not None:
             old.close()
+        self.graph = None   # a captured step refers to the old context
 
     def _resort_into_current_ctx(self):
         # the last sort is a pure function of pos_h: redo it in a new context
@@ -105,6 +142,40 @@ class Simulation:
         nv.sph_step(self.ctx, self.state, dt)
         if check:
             self._check_capacity()
+
+    # -- CUDA graph of one step --------------------------------------------------
+    def capture(self, dt):
+        """Capture one step (launch sequence of sph_step) into a CUDA graph.
+        Needs a previous step (so the step starts with the HFC at r_n)."""
+        if self.state.fresh:
+            raise RuntimeError("take one ordinary step before capturing")
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                nv.sph_step(self.ctx, self.state, dt, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = g
+        self.graph_dt = dt
+        return g
+
+    def replay(self, check=True):
+        """One step by replaying the captured graph (re-captured if the
+        context had to grow)."""
+        if self.graph is None:
+            self.capture(self.graph_dt)
+        self.graph.replay()
+        if check:
+            self._check_capacity()
+
+    def sim_slices(self, s):
+        """Column indices of simulation s of a batch (gas, then dark)."""
+        g0, g1 = int(self.gas_off[s]), int(self.gas_off[s + 1])
+        d0, d1 = int(self.dark_off[s]), int(self.dark_off[s + 1])
+        return np.concatenate([np.arange(g0, g1), self.n_gas + np.arange(d0, d1)])
 
     # -- host views -----------------------------------------------------------
     def positions(self):
