@@ -48,6 +48,22 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks (x itself with one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, n, steps, ms):
+    """Whole-job particle-steps/s: every rank advanced its own replica of n
+    particles by `steps` steps; the job took the slowest rank's `ms`."""
+    return world * n * steps / (ms / 1e3)
+
+
 def make_ic(name, rank=0):
     from paper_1807_08116_gb300 import ics
     g, d, halos, seed, _ = WORKLOADS[name]
@@ -255,11 +271,8 @@ def run_ours(args):
     stage = {name: float(np.mean([e.stage_ms()[name] for e in evs])) for name in nv.STAGES}
     for e in evs:
         e.close()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = aggregate_rate(world, n, args.steps, ms)
 
     # ---- end to end through the C ABI with host buffers --------------------
     e2e = None
@@ -327,12 +340,8 @@ def run_e2e(sim, args, dt, barrier, dist, world, n, ng):
         for k in ("r", "v", "e"):
             host[k].copy_(t[k], non_blocking=True)
         torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    if dist is not None:
-        x = torch.tensor([el], device="cuda")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        el = float(x.item())
-    return {"value": world * n * steps / el, "unit": "particle-steps/s",
+    el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    return {"value": aggregate_rate(world, n, steps, el * 1e3), "unit": "particle-steps/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": steps}
 
 
@@ -480,13 +489,56 @@ def run_serve(args):
     return 0
 
 
+def run_gravity(args):
+    """Gravity kernel alone on the two-halo construction with --n particles
+    (the same inputs the step uses): --warmup untimed and --steps timed
+    launches, CUDA events on the launching stream."""
+    import torch
+
+    from paper_1807_08116_gb300 import ics
+    from paper_1807_08116_gb300 import native as nv
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nv.lib()
+    q = args.n // 4
+    d = ics.two_halo(q, q, seed=2)
+    pm = np.empty((d["n"], 4), np.float32)
+    pm[:, :3] = d["r"]
+    pm[:, 3] = d["m"]
+    x = torch.as_tensor(pm, device="cuda")
+    out = torch.empty_like(x)
+    for _ in range(args.warmup):
+        nv.pp_gravity(x, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        nv.pp_gravity(x, out)
+    e1.record()
+    torch.cuda.synchronize()
+    if nv.pp_gravity_status():
+        raise RuntimeError("gravity kernel reported a timeout")
+    ms = e0.elapsed_time(e1) / args.steps
+    n = d["n"]
+    ips = float(n) * n / (ms / 1e3)
+    R, S = nv.sph_gravity_plan(n)
+    print(json.dumps({"metric": "PP interactions/s", "value": ips, "unit": "interactions/s",
+                      "n": n, "ms_per_launch": ms, "steps": args.steps, "warmup": args.warmup,
+                      "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12,
+                      "frac_of_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / FP32_PEAK_TFLOPS,
+                      "plan": {"targets_per_thread": R, "cluster_split": S}}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve"], default="large")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "gravity"],
+                    default="large")
+    ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity")
     ap.add_argument("--n-sims", type=int, default=64)
     ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--serve-window", type=float, default=90.0)
@@ -510,6 +562,8 @@ def main(argv=None):
         return run_ensemble(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "gravity":
+        return run_gravity(args)
     return run_ours(args)
 
 
