@@ -77,6 +77,8 @@ def _load():
             lib.oracle_gravity.argtypes = [I, P, D, D, P, I, P, P]
             lib.oracle_predict.argtypes = [I, I, D, P, P, P, P, P, P, P, P]
             lib.oracle_correct.argtypes = [I, I, D, P, P, P, P, P, P, P]
+            lib.oracle_cfl.restype = D
+            lib.oracle_cfl.argtypes = [I, P, P, P, P, P, P, P, I, P]
             for f in ("oracle_neighbor_counts", "oracle_neighbor_lists", "oracle_bin",
                       "oracle_counting_sort", "oracle_density", "oracle_hydro",
                       "oracle_gravity", "oracle_predict", "oracle_correct"):
@@ -202,6 +204,22 @@ def gravity(pos_m, G=DEFAULTS["G"], eps=DEFAULTS["eps"], rows=None):
     _load().oracle_gravity(n, _p(pos_m), float(G), float(eps), _p(rows), rows.shape[0],
                            _p(acc), _p(pot))
     return acc, pot
+
+
+def cfl_dt(pos_h, vel_e, rho, Q, E, C=0.5, gamma=DEFAULTS["gamma"], alpha=DEFAULTS["alpha"],
+           beta=DEFAULTS["beta"], eta=DEFAULTS["eta"], rows=None):
+    """Time step of Eq. 17: (min over rows, per-row bound).  Q: total
+    acceleration [n, 3]; E: de/dt [n]."""
+    pos_h = _c(pos_h, np.float32)
+    vel_e = _c(vel_e, np.float32)
+    rho = _c(rho, np.float32)
+    n = pos_h.shape[0]
+    rows = _rows(rows, n)
+    par = np.array([gamma, alpha, beta, eta, C], np.float64)
+    dt_row = np.empty(rows.shape[0], np.float64)
+    dt = _load().oracle_cfl(n, _p(pos_h), _p(vel_e), _p(rho), _p(_c(Q, np.float64)),
+                            _p(_c(E, np.float64)), _p(par), _p(rows), rows.shape[0], _p(dt_row))
+    return dt, dt_row
 
 
 # -- integrator ---------------------------------------------------------------

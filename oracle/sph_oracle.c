@@ -35,6 +35,10 @@
  *     predictor (Sect. 2.2, after Eq. 16).
  *  R9 order of particles inside one cell after the counting sort: ascending
  *     original index (a stable counting sort).
+ *  R10 in the time-step condition of Eq. 17, mu^max is the largest |mu_ij|
+ *     over the neighbours (mu_ij <= 0 as defined, so its plain maximum would
+ *     always be 0), c^max the largest c_ij and s^min the smallest |r_ij|; a
+ *     particle without neighbours sets no bound.
  */
 #include <math.h>
 #include <stdint.h>
@@ -417,4 +421,65 @@ void oracle_correct(int n, int n_gas, double dt, double *v, double *e,
         }
         if (i < n_gas) e[i] = 0.5 * (e_save[i] + e[i]) + 0.5 * dt * dedt[i];
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Modified CFL time step, Eq. 17 (reading R10), per listed gas particle:   */
+/* dt_i = C s_min / (c_max (1 + 1.2 alpha) + 1.2 beta mu_max               */
+/*                   + sqrt(s_min (|Q_i| + |E_i|)))                          */
+/* Q_i = total acceleration (hydro + gravity) [n][3], E_i = de_i/dt [n].    */
+/* par = {gamma, alpha, beta, eta, C}.  Returns min over the rows.          */
+/* ------------------------------------------------------------------------ */
+
+double oracle_cfl(int n, const float *pos_h, const float *vel_e, const float *rho,
+                  const double *Q, const double *E, const double *par, const int *rows,
+                  int n_rows, double *dt_row)
+{
+    double gam = par[0], alpha = par[1], beta = par[2], eta = par[3], C = par[4];
+    double dt_min = INFINITY;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(min:dt_min)
+    for (int r = 0; r < n_rows; ++r) {
+        int i = rows[r];
+        const float *pi = pos_h + 4 * (size_t)i;
+        const float *vi = vel_e + 4 * (size_t)i;
+        double p_i = (gam - 1.0) * (double)rho[i] * (double)vi[3];
+        double c_i = p_i >= 0.0 ? sqrt(gam * p_i / (double)rho[i]) : 0.0;
+        double s_min = INFINITY, c_max = 0.0, mu_max = 0.0;
+        int found = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const float *pj = pos_h + 4 * (size_t)j;
+            if (!nb_pred(pi, pj)) continue;
+            const float *vj = vel_e + 4 * (size_t)j;
+            found = 1;
+            double dx = (double)pi[0] - (double)pj[0];
+            double dy = (double)pi[1] - (double)pj[1];
+            double dz = (double)pi[2] - (double)pj[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double rr = sqrt(r2);
+            if (rr < s_min) s_min = rr;
+            double p_j = (gam - 1.0) * (double)rho[j] * (double)vj[3];
+            double c_j = p_j >= 0.0 ? sqrt(gam * p_j / (double)rho[j]) : 0.0;
+            double c_ij = 0.5 * (c_i + c_j);
+            if (c_ij > c_max) c_max = c_ij;
+            double rv = dx * ((double)vi[0] - (double)vj[0]) + dy * ((double)vi[1] - (double)vj[1]) +
+                        dz * ((double)vi[2] - (double)vj[2]);
+            if (rv < 0.0) {
+                double hij = 0.5 * ((double)pi[3] + (double)pj[3]);
+                double mu = hij * rv / (r2 + eta * hij * hij);
+                if (-mu > mu_max) mu_max = -mu;
+            }
+        }
+        double dt = INFINITY;
+        if (found) {
+            const double *q = Q + 3 * (size_t)i;
+            double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+            double denom = c_max * (1.0 + 1.2 * alpha) + 1.2 * beta * mu_max +
+                           sqrt(s_min * (qn + fabs(E[i])));
+            dt = C * s_min / denom;
+        }
+        dt_row[r] = dt;
+        if (dt < dt_min) dt_min = dt;
+    }
+    return dt_min;
 }
