@@ -202,6 +202,21 @@ int sph_density(sph_ctx *ctx, int32_t n_gas, const float *d_mass, float *d_rho,
 int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
                const float *d_mass, float *d_acc_dedt, sph_stream_t stream);
 
+/* Time step of the modified CFL condition, Eq. 17, for the gas particles of
+ * the last sort and lists: dt_i = C s_min / (c_max (1 + 1.2 alpha) +
+ * 1.2 beta mu_max + sqrt(s_min (|Q_i| + |E_i|))) with s_min the smallest
+ * |r_ij|, c_max the largest c_ij and mu_max the largest |mu_ij| over the
+ * neighbours (mu_ij <= 0 as defined, so its magnitude is meant), Q_i =
+ * |a_hyd + g|, E_i = |de/dt|; a particle without neighbours sets no bound.
+ * Inputs in original order: d_vel_e, d_rho, d_mass as for sph_forces,
+ * d_acc_hyd[n_gas][4] and d_grav (at least n_gas float4; the gas part of a
+ * state's grav).  Writes min_i dt_i to the device float *d_dt_min (+inf if
+ * no particle is bounded) and, if d_dt_particle != NULL, every dt_i
+ * (original order).  FP32. */
+int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+               const float *d_mass, const float *d_acc_hyd, const float *d_grav, float C_cfl,
+               float *d_dt_particle, float *d_dt_min, sph_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Stage GFC: direct particle-particle gravity (Eq. 4).                      */
 /* ------------------------------------------------------------------------ */

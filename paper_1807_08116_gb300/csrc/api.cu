@@ -395,6 +395,26 @@ extern "C" int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, con
                          ctx->nb_idx, (int)ctx->capacity, n_gas, hp, reinterpret_cast<float4 *>(d_acc_dedt), st);
 }
 
+extern "C" int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+                          const float *d_mass, const float *d_acc_hyd, const float *d_grav,
+                          float C_cfl, float *d_dt_particle, float *d_dt_min, sph_stream_t stream) {
+    if (!ctx || n_gas != ctx->n_sorted || !ctx->nb_built || !d_dt_min || !(C_cfl > 0.0f))
+        return SPH_ERR_INVALID_ARG;
+    if (n_gas > 0 && (!d_vel_e || !d_rho || !d_mass || !d_acc_hyd || !d_grav || !aligned16(d_vel_e) ||
+                      !aligned16(d_acc_hyd) || !aligned16(d_grav)))
+        return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HydroParams hp = hydro_params(ctx);
+    int rc;
+    if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
+        return rc;
+    return launch_cfl(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start, ctx->nb_idx,
+                      (int)ctx->capacity, n_gas, hp, C_cfl,
+                      reinterpret_cast<const float4 *>(d_acc_hyd),
+                      reinterpret_cast<const float4 *>(d_grav), d_dt_particle, d_dt_min, st);
+}
+
 // ---------------------------------------------------------------------------
 // Whole steps
 // ---------------------------------------------------------------------------

@@ -44,9 +44,7 @@ namespace sphgb {
 #ifndef SPHGB_GR_MINB
 #define SPHGB_GR_MINB 2
 #endif
-#ifndef SPHGB_GR_RCP
-#define SPHGB_GR_RCP 0
-#endif
+
 constexpr int GR_THREADS = SPHGB_GR_THREADS;
 constexpr int GR_UNROLL = SPHGB_GR_UNROLL;
 constexpr int GR_TJ = SPHGB_GR_TJ;                 // sources per tile
@@ -104,12 +102,6 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned
         : "memory");
 }
 
-__device__ __forceinline__ float rcp_mufu(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 __device__ __forceinline__ float rsqrt_mufu(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -158,17 +150,9 @@ __device__ __forceinline__ void tile_sums(const float4 *__restrict__ dup, int cn
                 inv.y = r2.y > 0.f ? inv.y : 0.f;
             }
             const float2 s = __fmul2_rn(qm, inv);
-#if SPHGB_GR_RCP
-            // m / r^3 = (m / r) * (1 / r^2): a second MUFU op instead of an FMUL
-            float2 inv2 = make_float2(rcp_mufu(r2.x), rcp_mufu(r2.y));
-            if (GUARD) {
-                inv2.x = r2.x > 0.f ? inv2.x : 0.f;
-                inv2.y = r2.y > 0.f ? inv2.y : 0.f;
-            }
-            const float2 s3 = __fmul2_rn(s, inv2);
-#else
+            // m / r^3 with two more FMUL2: a second MUFU op (1 / r^2) instead
+            // was measured slower -- MUFU issues at a quarter of the FP32 rate
             const float2 s3 = __fmul2_rn(__fmul2_rn(s, inv), inv);
-#endif
             sx[p] = __ffma2_rn(s3, dx, sx[p]);
             sy[p] = __ffma2_rn(s3, dy, sy[p]);
             sz[p] = __ffma2_rn(s3, dz, sz[p]);

@@ -127,6 +127,82 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
     acc_out[perm[i]] = make_float4(ax.value(), ay.value(), az.value(), de.value());
 }
 
+// Time step of Eq. 17 per gas particle, and its minimum.  mu^max is the
+// largest |mu_ij| over the neighbours (mu_ij <= 0 as defined), c^max the
+// largest c_ij, s^min the smallest |r_ij|; Q_i = |a_hyd + g|, E_i = |de/dt|.
+__global__ void __launch_bounds__(128)
+cfl_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
+           const float4 *__restrict__ aux_s, const int *__restrict__ perm,
+           const int *__restrict__ nb_start, const int *__restrict__ nb_idx, int cap, int n,
+           HydroParams hp, float C, const float4 *__restrict__ acc_hyd,
+           const float4 *__restrict__ grav, float *__restrict__ dt_out,
+           unsigned *__restrict__ dt_min_bits) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float dt = __int_as_float(0x7f800000);   // +inf: no bound
+    if (i < n) {
+        const float4 p = pos_h_s[i];
+        const float4 v = vel_s[i];
+        const float ci = aux_s[i].w;
+        float s_min = dt, c_max = 0.0f, mu_max = 0.0f;
+        const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+        for (int k = b; k < e; ++k) {
+            const int j = nb_idx[k];
+            if ((unsigned)j >= (unsigned)n) continue;
+            const float4 q = pos_h_s[j];
+            const float4 w = vel_s[j];
+            const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            s_min = fminf(s_min, sqrtf(r2));
+            c_max = fmaxf(c_max, 0.5f * (ci + aux_s[j].w));
+            const float rv = fmaf(dx, v.x - w.x, fmaf(dy, v.y - w.y, dz * (v.z - w.z)));
+            if (rv < 0.0f) {
+                const float hij = 0.5f * (p.w + q.w);
+                mu_max = fmaxf(mu_max, -hij * rv / fmaf(hp.eta * hij, hij, r2));
+            }
+        }
+        const int oi = perm[i];
+        if (e > b) {
+            const float4 a = acc_hyd[oi], g = grav[oi];
+            const float qx = a.x + g.x, qy = a.y + g.y, qz = a.z + g.z;
+            const float qn = sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+            const float den = c_max * (1.0f + 1.2f * hp.alpha) + 1.2f * hp.beta * mu_max +
+                              sqrtf(s_min * (qn + fabsf(a.w)));
+            dt = C * s_min / den;
+        }
+        if (dt_out) dt_out[oi] = dt;
+    }
+    // block minimum, then one atomic per block (dt >= 0: the bits order like the values)
+    __shared__ float s_min_dt[4];
+    float m = dt;
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_min_dt[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, s_min_dt[w]);
+        if (m >= 0.0f) atomicMin(dt_min_bits, __float_as_uint(m));
+    }
+}
+
+__global__ void fill_u32_kernel(unsigned *p, unsigned v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, const int *perm,
+               const int *nb_start, const int *nb_idx, int cap, int n, HydroParams hp, float C,
+               const float4 *acc_hyd, const float4 *grav, float *dt_out, float *dt_min,
+               cudaStream_t st) {
+    fill_u32_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned *>(dt_min), 0x7f800000u);
+    note_launch();
+    if (n > 0) {
+        cfl_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx,
+                                                    cap, n, hp, C, acc_hyd, grav, dt_out,
+                                                    reinterpret_cast<unsigned *>(dt_min));
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
 int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, const int *nb_start,
                    const int *nb_idx, int cap, int n, float sigma, float *rho_s, float *rho_out,
                    float *h_next_out, float *mass_s, cudaStream_t st) {

@@ -59,6 +59,10 @@ int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, co
                    float *h_next_out, float *mass_s, cudaStream_t st);
 int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
                       int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st);
+int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, const int *perm,
+               const int *nb_start, const int *nb_idx, int cap, int n, HydroParams hp, float C,
+               const float4 *acc_hyd, const float4 *grav, float *dt_out, float *dt_min,
+               cudaStream_t st);
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
                   HydroParams hp,

@@ -120,6 +120,7 @@ def lib():
             "sph_build_neighbors": (_I, [_P, _I, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
             "sph_density": (_I, [_P, _I, _P, _P, _P, _P]),
             "sph_forces": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+            "sph_cfl_dt": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
             "pp_gravity": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "pp_gravity_status": (_I, [_P, ctypes.POINTER(_I)]),
             "sph_gravity_plan": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
@@ -308,6 +309,21 @@ def sph_forces(ctx, vel_e, rho, mass, acc_dedt, stream=None):
                           _ptr(mass, torch.float32, (n,), "mass"),
                           _ptr(acc_dedt, torch.float32, (n, 4), "acc_dedt"), _stream(stream))
     _check("sph_forces", rc)
+
+
+def sph_cfl_dt(ctx, vel_e, rho, mass, acc_hyd, grav, C, dt_min, dt_particle=None, stream=None):
+    """Eq. 17 time step; grav may hold more rows than the gas (a state's grav)."""
+    n = vel_e.shape[0]
+    if grav.shape[0] < n or tuple(grav.shape[1:]) != (4,):
+        raise ValueError("grav must have at least n_gas rows of 4")
+    rc = lib().sph_cfl_dt(ctx.handle, n, _ptr(vel_e, torch.float32, (n, 4), "vel_e"),
+                          _ptr(rho, torch.float32, (n,), "rho"),
+                          _ptr(mass, torch.float32, (n,), "mass"),
+                          _ptr(acc_hyd, torch.float32, (n, 4), "acc_hyd"),
+                          _ptr(grav, torch.float32, None, "grav"), float(C),
+                          _ptr(dt_particle, torch.float32, (n,), "dt_particle", True),
+                          _ptr(dt_min, torch.float32, (1,), "dt_min"), _stream(stream))
+    _check("sph_cfl_dt", rc)
 
 
 def pp_gravity(pos_m, acc_pot, G=1.0, eps=0.01, flags=0, stream=None):

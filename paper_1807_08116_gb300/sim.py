@@ -177,6 +177,18 @@ class Simulation:
         d0, d1 = int(self.dark_off[s]), int(self.dark_off[s + 1])
         return np.concatenate([np.arange(g0, g1), self.n_gas + np.arange(d0, d1)])
 
+    def cfl_dt(self, C=0.5):
+        """Next time step from the modified CFL condition (Eq. 17) at the
+        current state (lists, density and forces of the last evaluation)."""
+        if self.n_gas == 0:
+            return float("inf")
+        if not hasattr(self, "_dt_min"):
+            self._dt_min = torch.empty(1, dtype=torch.float32, device=self.device)
+        t = self.t
+        nv.sph_cfl_dt(self.ctx, t["vel_e"], t["rho"], t["mass"][:self.n_gas], t["acc_hyd"],
+                      t["grav"], C, self._dt_min)
+        return float(self._dt_min.item())
+
     # -- host views -----------------------------------------------------------
     def positions(self):
         return self.t["r"].view(3, self.n).T.cpu().numpy()

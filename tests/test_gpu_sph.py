@@ -152,3 +152,35 @@ def test_isolated_and_empty():
     nv.sph_density(ctx, e, e.clone(), e.clone())
     nv.sph_forces(ctx, z, e, e.clone(), z.clone())
     torch.cuda.synchronize()
+
+
+def test_cfl_time_step(orc):
+    # Eq. 17 per particle and its minimum, on stirred gas with forces
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    d = ics.single_halo(6000, 0, seed=51)
+    ph, mass, ve = _stirred(d, seed=3)
+    n = len(ph)
+    orho, _ = orc.density(ph, mass)
+    rho = orho.astype(np.float32)
+    rng = np.random.default_rng(4)
+    acc = rng.normal(size=(n, 4)).astype(np.float32)
+    grav = rng.normal(size=(n, 4)).astype(np.float32)
+    ctx = nv.Ctx(n, 200 * n)
+    nv.sph_bin_and_sort(ctx, torch.as_tensor(ph, device="cuda"))
+    nv.sph_build_neighbors(ctx, n)
+    dt_min = torch.empty(1, device="cuda")
+    dt_p = torch.empty(n, device="cuda")
+    cu = lambda a: torch.as_tensor(a, device="cuda")
+    nv.sph_cfl_dt(ctx, cu(ve), cu(rho), cu(mass), cu(acc), cu(grav), 0.6, dt_min, dt_p)
+    torch.cuda.synchronize()
+    Q = acc[:, :3].astype(np.float64) + grav[:, :3].astype(np.float64)
+    E = acc[:, 3].astype(np.float64)
+    odt, orow = orc.cfl_dt(ph, ve, rho, Q, E, C=0.6)
+    got = dt_p.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(orow)
+    assert np.array_equal(np.isfinite(got), fin)
+    rel = np.abs(got[fin] - orow[fin]) / orow[fin]
+    print(f"cfl dt: max rel {rel.max():.2e}; min {odt:.4e}")
+    assert rel.max() < 1e-5
+    assert abs(float(dt_min.item()) - odt) < 1e-5 * odt

@@ -136,3 +136,20 @@ def test_rerun_is_bitwise_identical():
         outs.append((sim.positions(), sim.velocities(), sim.t["e"].cpu().numpy()))
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def test_step_size_from_cfl_condition(orc):
+    need_gpu()
+    from paper_1807_08116_gb300.sim import Simulation
+    d = ics.single_halo(4096, 4096, seed=6)
+    sim = Simulation(d)
+    sim.initial_rhs()
+    dt = sim.cfl_dt(0.5)
+    ref = orc.OracleSim(d["r"].T, d["v"].T, d["e"], d["m"], d["h"], d["n_gas"])
+    ref.initial_rhs()
+    ng = d["n_gas"]
+    Q = ref.a_hyd + ref.grav[:ng]
+    odt, _ = orc.cfl_dt(ref.pos_h(), ref.vel_e(), ref.rho.astype(np.float32), Q, ref.dedt, C=0.5)
+    assert 0 < dt < 1
+    assert abs(dt - odt) < 1e-4 * odt
+    sim.step(dt)      # and the step accepts it
