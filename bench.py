@@ -380,14 +380,8 @@ def run_ensemble(args):
     # (a) batched
     bsim = Simulation(ic, batch_offsets=(go, do, so))
     bsim.initial_rhs()
-    tune = {}
-    pm, out = bsim.t["pos_m"], torch.empty_like(bsim.t["pos_m"])
-    for R in (2, 4, 8):
-        bsim.batch.set_plan(R)
-        nv.pp_gravity_batched(bsim.batch, pm, out)
-        tune[R] = timed(lambda: nv.pp_gravity_batched(bsim.batch, pm, out), 3) / 3
-    best_R = min(tune, key=tune.get)
-    bsim.batch.set_plan(best_R)
+    from paper_1807_08116_gb300.tune import tune_batch
+    best_R, tune = tune_batch(bsim.batch, bsim.t["pos_m"], reps=3)
     for _ in range(args.warmup):
         bsim.step(dt)
     bsim.capture(dt)

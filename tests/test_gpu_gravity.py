@@ -136,3 +136,22 @@ def test_every_launch_plan(orc, R, S):
     assert rms <= RMS_TOL and mx <= MAX_TOL, (R, S, rms, mx)
     prms, pmx = err(g[:, 3:], pot[:, None])
     assert prms <= RMS_TOL and pmx <= MAX_TOL
+
+
+def test_autotuner_picks_a_timed_plan(orc):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.tune import tune_gravity
+    rng = np.random.default_rng(12)
+    pm = pos_m_of(rng.normal(size=(20000, 3)), np.full(20000, 5e-5))
+    x = torch.as_tensor(pm, device="cuda")
+    try:
+        best, res = tune_gravity(x, reps=1)
+        assert best in res and res[best] == min(res.values())
+        assert nv.sph_gravity_plan(20000) == best
+        g = _gpu_gravity(pm)
+    finally:
+        nv.sph_gravity_tune(0)
+    acc, _ = orc.gravity(pm)
+    rms, mx = err(g[:, :3], acc)
+    assert rms <= RMS_TOL and mx <= MAX_TOL
