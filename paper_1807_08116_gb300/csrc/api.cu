@@ -60,6 +60,7 @@ struct sph_ctx {
     // carved arrays
     int *key, *count, *start, *perm, *tmp, *long_list, *long_count;
     unsigned *hmax_cell;
+    unsigned *occ;   // super-cell occupancy bits, 2^(log2_M + 1) bits
     int *lvl_count;
     unsigned *lvl_hmax;
     GridDev *grid;
@@ -112,6 +113,7 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->count = cv.take<int>(M);
     c->start = cv.take<int>(M + 1);
     c->hmax_cell = cv.take<unsigned>(M);
+    c->occ = cv.take<unsigned>(M / 16 + 1);
     c->perm = cv.take<int>(n);
     c->tmp = cv.take<int>(c->capacity > (long long)n ? (size_t)c->capacity : n);
     c->long_list = cv.take<int>(seg_list);
@@ -269,13 +271,14 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
     // SP0: zero the per-bucket and per-level arrays
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)M, st));
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->hmax_cell, 0, sizeof(unsigned) * (size_t)M, st));
+    SPH_CUDA_TRY(cudaMemsetAsync(ctx->occ, 0, sizeof(unsigned) * ((size_t)M / 16 + 1), st));
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_count, 0, sizeof(int) * kMaxLevels, st));
     SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
     // SP1
     const int *sim_of = ctx->batch ? ctx->batch->d_sim_of_gas : nullptr;
     if (sim_of && n_gas != ctx->batch->n_gas) return SPH_ERR_INVALID_ARG;
-    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->key, ctx->count, ctx->hmax_cell,
-                         ctx->lvl_count, ctx->lvl_hmax, st)))
+    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->occ, ctx->log2_M + 1, ctx->key,
+                         ctx->count, ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
         return rc;
     // SP2 + SP3
     if ((rc = launch_scan_exclusive(ctx->count, M, ctx->start, ctx->block_sums, st))) return rc;
@@ -319,6 +322,8 @@ extern "C" int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_st
     a.lvl_hmax = ctx->lvl_hmax;
     a.grid = ctx->grid;
     a.sim_s = ctx->sorted_batched ? ctx->sim_s : nullptr;
+    a.occ = ctx->occ;
+    a.log2_B = ctx->log2_M + 1;
     a.n = n;
     a.own = ctx->own;
     a.rev = ctx->rev;

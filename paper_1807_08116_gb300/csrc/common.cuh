@@ -68,6 +68,17 @@ __device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2
     return (int)(k & ((1ull << log2_M) - 1ull));
 }
 
+// Occupancy bit of a super-cell (8 x 8 x 8 cells of one level): set by the
+// binning for every occupied super-cell, read by the neighbour search to skip
+// levels with nobody near.  Hash collisions only cost a wasted probe.
+constexpr int kSuperShift = 3;
+constexpr unsigned long long kSuperSalt = 0xD1B54A32D192ED03ull;
+__device__ __forceinline__ unsigned super_bit(int sx, int sy, int sz, int l, int log2_B) {
+    unsigned long long m = spread3((unsigned)sx) | (spread3((unsigned)sy) << 1) |
+                           (spread3((unsigned)sz) << 2);
+    return (unsigned)((m + (unsigned long long)(l + 1) * kSuperSalt) & ((1ull << log2_B) - 1ull));
+}
+
 // FP32 neighbour predicate: ((dx*dx + dy*dy) + dz*dz) < (h_i + h_j)^2,
 // every operation rounded separately.
 __device__ __forceinline__ bool nb_pred(float4 a, float4 b) {

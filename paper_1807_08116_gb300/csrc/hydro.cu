@@ -42,6 +42,7 @@ density_kernel(const float4 *__restrict__ pos_h_s, const float *__restrict__ mas
     }
     // rows are clipped to the list capacity (an overflowed build is flagged)
     const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+#pragma unroll 4
     for (int k = b; k < e; ++k) {
         const int j = nb_idx[k];
         if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
@@ -94,6 +95,7 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
     ax.init(); ay.init(); az.init(); de.init();
     // rows are clipped to the list capacity (an overflowed build is flagged)
     const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+#pragma unroll 4
     for (int k = b; k < e; ++k) {
         const int j = nb_idx[k];
         if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
@@ -145,7 +147,8 @@ cfl_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
         const float ci = aux_s[i].w;
         float s_min = dt, c_max = 0.0f, mu_max = 0.0f;
         const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
-        for (int k = b; k < e; ++k) {
+    #pragma unroll 4
+    for (int k = b; k < e; ++k) {
             const int j = nb_idx[k];
             if ((unsigned)j >= (unsigned)n) continue;
             const float4 q = pos_h_s[j];

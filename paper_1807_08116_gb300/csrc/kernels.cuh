@@ -15,9 +15,9 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
 int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
                      cudaStream_t st);
 int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st);
-int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
-               int *count, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
-               cudaStream_t st);
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, unsigned *occ,
+               int log2_B, int *key, int *count, unsigned *hmax_cell, int *lvl_count,
+               unsigned *lvl_hmax, cudaStream_t st);
 int launch_gather_int(const int *src, const int *perm, int n, int *dst, cudaStream_t st);
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
 int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st);
@@ -38,6 +38,8 @@ struct NbArgs {
     const unsigned *lvl_hmax;
     const GridDev *grid;
     const int *sim_s;        // [n] simulation of each sorted particle, or NULL (one simulation)
+    const unsigned *occ;     // super-cell occupancy bits, or NULL
+    int log2_B;
     int n;
     int *own;                // [n] own-search count
     int *rev;                // [n] reverse count / cursor

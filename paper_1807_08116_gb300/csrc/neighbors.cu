@@ -57,6 +57,18 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
             set_flag(a.flags, SPH_FLAG_SEARCH_WIDE);
             continue;
         }
+        if (a.occ && l > li) {
+            // skip the level when none of the super-cells the box touches holds
+            // a particle of it (the particle's own level is always occupied)
+            bool any = false;
+            for (int sz = lz >> kSuperShift; sz <= (hz >> kSuperShift) && !any; ++sz)
+                for (int sy = ly >> kSuperShift; sy <= (hy >> kSuperShift) && !any; ++sy)
+                    for (int sx = lx >> kSuperShift; sx <= (hx >> kSuperShift) && !any; ++sx) {
+                        const unsigned bit = super_bit(sx, sy, sz, l + kMaxLevels * si, a.log2_B);
+                        any = (a.occ[bit >> 5] >> (bit & 31)) & 1u;
+                    }
+            if (!any) continue;
+        }
         for (int cz = lz; cz <= hz; ++cz)
             for (int cy = ly; cy <= hy; ++cy)
                 for (int cx = lx; cx <= hx; ++cx) {

@@ -108,7 +108,7 @@ extern "C" int sph_bin_and_sort_noalloc(const float *d_pos_h, int32_t n_gas, int
     SPH_CUDA_TRY(cudaMemsetAsync(hmax, 0, sizeof(unsigned) * (size_t)M, st));
     SPH_CUDA_TRY(cudaMemsetAsync(lvl_count, 0, sizeof(int) * kMaxLevels, st));
     SPH_CUDA_TRY(cudaMemsetAsync(lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
-    if ((rc = launch_bin(pos, nullptr, n_gas, grid, d_key, count, hmax, lvl_count, lvl_hmax, st))) return rc;
+    if ((rc = launch_bin(pos, nullptr, n_gas, grid, nullptr, 0, d_key, count, hmax, lvl_count, lvl_hmax, st))) return rc;
     if ((rc = launch_scan_exclusive(count, M, d_cell_start, block_sums, st))) return rc;
     if ((rc = launch_scatter(d_key, n_gas, d_cell_start, count, d_perm, st))) return rc;
     return launch_segsort_buckets(d_cell_start, M, d_perm, tmp, long_list, long_count, st);

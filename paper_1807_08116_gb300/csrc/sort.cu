@@ -104,8 +104,8 @@ __global__ void grid_set_kernel(GridDev g, GridDev *grid) {
 // ---------------------------------------------------------------------------
 
 __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restrict__ sim_of, int n,
-                           const GridDev *__restrict__ gridp, int *__restrict__ key,
-                           int *__restrict__ count,
+                           const GridDev *__restrict__ gridp, unsigned *__restrict__ occ, int log2_B,
+                           int *__restrict__ key, int *__restrict__ count,
                            unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
                            unsigned *__restrict__ lvl_hmax) {
     __shared__ int s_cnt[kMaxLevels];
@@ -129,6 +129,11 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restri
         const int sim = sim_of ? sim_of[i] : 0;
         int k = bucket_of(cx, cy, cz, l + kMaxLevels * sim, g.log2_M);
         key[i] = k;
+        if (occ) {
+            const unsigned b = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
+                                         l + kMaxLevels * sim, log2_B);
+            atomicOr(&occ[b >> 5], 1u << (b & 31));
+        }
         atomicAdd(&count[k], 1);
         unsigned hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
         atomicMax(&hmax_cell[k], hb);
@@ -457,12 +462,12 @@ int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st) {
     return SPH_OK;
 }
 
-int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
-               int *count, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
-               cudaStream_t st) {
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, unsigned *occ,
+               int log2_B, int *key, int *count, unsigned *hmax_cell, int *lvl_count,
+               unsigned *lvl_hmax, cudaStream_t st) {
     if (n > 0) {
-        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, n, grid, key, count, hmax_cell,
-                                                       lvl_count, lvl_hmax);
+        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, n, grid, occ, log2_B, key,
+                                                       count, hmax_cell, lvl_count, lvl_hmax);
         note_launch();
     }
     SPH_LAUNCH_CHECK();
