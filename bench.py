@@ -562,7 +562,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=512,
                     help="target rows per stage of each reference-arm step sample")
-    ap.add_argument("--cpu-rows", type=int, default=2048,
+    ap.add_argument("--cpu-rows", type=int, default=8192,
                     help="target rows per stage of the cpu_baseline sample")
     ap.add_argument("--gfc-traffic", type=float, default=None,
                     help="DRAM bytes per gravity launch from an ncu capture of this workload")
