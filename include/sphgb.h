@@ -95,6 +95,11 @@ int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_t log2_M,
 /* Release the host-side handle (not the workspace). */
 int sph_ctx_destroy(sph_ctx *ctx);
 
+/* Lanes that share one neighbour row in the density and force kernels
+ * (1, 2, 4 or 8; default 4): a tuning knob, results differ only in the
+ * order of the per-lane partial sums. */
+int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes);
+
 /* Replace the model constants used by later calls. */
 int sph_ctx_set_params(sph_ctx *ctx, const SphParams *params);
 

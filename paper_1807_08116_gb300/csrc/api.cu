@@ -74,6 +74,7 @@ struct sph_ctx {
     int n_sorted;    // n_gas of the last sort
     int nb_built;    // 1 once lists match the last sort
     int sorted_batched;        // the last sort used the batch's simulation map
+    int hydro_lanes;           // lanes per row in DC / HFC (1, 2, 4 or 8)
     const sph_batch *batch;    // NULL: one simulation
 };
 
@@ -187,6 +188,7 @@ extern "C" int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_
     c->capacity = nb_capacity;
     c->ws = d_workspace;
     c->ws_bytes = workspace_bytes;
+    c->hydro_lanes = 4;
     size_t total = 0;
     carve(c, static_cast<char *>(d_workspace), &total);
     if (cudaMemsetAsync(d_workspace, 0, total, (cudaStream_t)stream) != cudaSuccess) {
@@ -199,6 +201,12 @@ extern "C" int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_
 
 extern "C" int sph_ctx_destroy(sph_ctx *ctx) {
     delete ctx;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes) {
+    if (!ctx || (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)) return SPH_ERR_INVALID_ARG;
+    ctx->hydro_lanes = lanes;
     return SPH_OK;
 }
 
@@ -379,9 +387,8 @@ extern "C" int sph_density(sph_ctx *ctx, int32_t n_gas, const float *d_mass, flo
     if (!ctx || n_gas != ctx->n_sorted || !ctx->nb_built) return SPH_ERR_INVALID_ARG;
     if (n_gas > 0 && (!d_mass || !d_rho || !d_h_next)) return SPH_ERR_INVALID_ARG;
     return launch_density(ctx->pos_h_s, d_mass, ctx->perm, ctx->nb_start, ctx->nb_idx,
-                          (int)ctx->capacity, n_gas,
-                          ctx->params.sigma, ctx->rho_s, d_rho, d_h_next, ctx->mass_s,
-                          (cudaStream_t)stream);
+                          (int)ctx->capacity, n_gas, ctx->params.sigma, ctx->hydro_lanes,
+                          ctx->rho_s, d_rho, d_h_next, ctx->mass_s, (cudaStream_t)stream);
 }
 
 extern "C" int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
@@ -397,7 +404,8 @@ extern "C" int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, con
                                 n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
         return rc;
     return launch_forces(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
-                         ctx->nb_idx, (int)ctx->capacity, n_gas, hp, reinterpret_cast<float4 *>(d_acc_dedt), st);
+                         ctx->nb_idx, (int)ctx->capacity, n_gas, hp, ctx->hydro_lanes,
+                         reinterpret_cast<float4 *>(d_acc_dedt), st);
 }
 
 extern "C" int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,

@@ -21,44 +21,71 @@ __device__ __forceinline__ float spline_shape(float xi) {
     return xi < 2.0f ? 0.25f * t * t * t : 0.0f;
 }
 
+// Lanes of one row's group: G consecutive lanes of a warp (G divides 32).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31u;
+    return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+}
+
+// Fixed-shape tree sum over the G lanes of a group (same order every run).
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+// Density of Eq. 7: G lanes share one sorted row; lane q takes neighbours
+// q, q + G, ... with its own compensated sum; the group adds the partials.
+template <int G>
 __global__ void __launch_bounds__(128)
-density_kernel(const float4 *__restrict__ pos_h_s, const float *__restrict__ mass,
+density_kernel(const float4 *__restrict__ pos_h_s, const float *__restrict__ mass_s,
                const int *__restrict__ perm, const int *__restrict__ nb_start,
                const int *__restrict__ nb_idx, int cap, int n, float sigma,
-               float *__restrict__ rho_s,
-               float *__restrict__ rho_out, float *__restrict__ h_next_out,
-               float *__restrict__ mass_s) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int oi = perm[i];
+               float *__restrict__ rho_s, float *__restrict__ rho_out,
+               float *__restrict__ h_next_out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / G, q = t % G;
+    if (i >= n) return;   // whole groups leave together (G divides the block)
+    const unsigned mask = group_mask<G>();
     const float4 p = pos_h_s[i];
-    const float mi = mass[oi];
+    const float mi = mass_s[i];
     const float hi = p.w;
     Kahan acc;
     acc.init();
-    {
+    if (q == 0) {
         float ih = 1.0f / hi;
         acc.add(mi * (ih * ih * ih) * kInvPi);   // self term m_i W(0, h_i)
     }
     // rows are clipped to the list capacity (an overflowed build is flagged)
     const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
 #pragma unroll 4
-    for (int k = b; k < e; ++k) {
+    for (int k = b + q; k < e; k += G) {
         const int j = nb_idx[k];
         if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
-        const float4 q = pos_h_s[j];
-        const float mj = mass[perm[j]];
-        float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        const float4 o = pos_h_s[j];
+        const float mj = mass_s[j];
+        float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
         float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        float hij = 0.5f * (hi + q.w);
+        float hij = 0.5f * (hi + o.w);
         float ih = 1.0f / hij;
         acc.add(mj * (ih * ih * ih) * kInvPi * spline_shape(r * ih));
     }
-    const float rho = acc.value();
-    rho_s[i] = rho;
-    mass_s[i] = mi;
-    rho_out[oi] = rho;
-    h_next_out[oi] = sigma * cbrtf(mi / rho);
+    const float rho = group_sum<G>(acc.s - acc.c, mask);
+    if (q == 0) {
+        const int oi = perm[i];
+        rho_s[i] = rho;
+        rho_out[oi] = rho;
+        h_next_out[oi] = sigma * cbrtf(mi / rho);
+    }
+}
+
+__global__ void gather_mass_kernel(const float *__restrict__ mass, const int *__restrict__ perm,
+                                   int n, float *__restrict__ mass_s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) mass_s[j] = mass[perm[j]];
 }
 
 // Sorted working copies for HFC: vel_s = (vx, vy, vz, e); aux_s = (m, rho,
@@ -79,13 +106,17 @@ __global__ void hydro_prep_kernel(const float4 *__restrict__ vel_e, const float 
     aux_s[j] = make_float4(mass[o], r, P, c);
 }
 
+// Hydrodynamic acceleration and heating of Eqs. 10-11, G lanes per row.
+template <int G>
 __global__ void __launch_bounds__(128)
 forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
               const float4 *__restrict__ aux_s, const int *__restrict__ perm,
               const int *__restrict__ nb_start, const int *__restrict__ nb_idx, int cap, int n,
               HydroParams hp, float4 *__restrict__ acc_out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / G, q = t % G;
     if (i >= n) return;
+    const unsigned mask = group_mask<G>();
     const float4 p = pos_h_s[i];
     const float4 v = vel_s[i];
     const float4 ai = aux_s[i];
@@ -96,21 +127,21 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
     // rows are clipped to the list capacity (an overflowed build is flagged)
     const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
 #pragma unroll 4
-    for (int k = b; k < e; ++k) {
+    for (int k = b + q; k < e; k += G) {
         const int j = nb_idx[k];
         if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
-        const float4 q = pos_h_s[j];
+        const float4 o = pos_h_s[j];
         const float4 w = vel_s[j];
         const float4 aj = aux_s[j];
-        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
         const float dvx = v.x - w.x, dvy = v.y - w.y, dvz = v.z - w.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float r = sqrtf(r2);
-        const float hij = 0.5f * (p.w + q.w);
+        const float hij = 0.5f * (p.w + o.w);
         const float ih = 1.0f / hij;
-        const float t = fmaxf(2.0f - r * ih, 0.0f);
+        const float tt = fmaxf(2.0f - r * ih, 0.0f);
         // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
-        const float f = r > 0.0f ? kdw * (ih * ih * ih) * t * t * ih / r : 0.0f;
+        const float f = r > 0.0f ? kdw * (ih * ih * ih) * tt * tt * ih / r : 0.0f;
         const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
         float nu = 0.0f;
         if (rv < 0.0f) {
@@ -126,7 +157,11 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
         az.add(-g * dz);
         de.add(0.5f * g * fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz)));
     }
-    acc_out[perm[i]] = make_float4(ax.value(), ay.value(), az.value(), de.value());
+    const float sx = group_sum<G>(ax.s - ax.c, mask);
+    const float sy = group_sum<G>(ay.s - ay.c, mask);
+    const float sz = group_sum<G>(az.s - az.c, mask);
+    const float se = group_sum<G>(de.s - de.c, mask);
+    if (q == 0) acc_out[perm[i]] = make_float4(sx, sy, sz, se);
 }
 
 // Time step of Eq. 17 per gas particle, and its minimum.  mu^max is the
@@ -206,13 +241,21 @@ int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, 
     return SPH_OK;
 }
 
+static unsigned grid_for(long long threads) { return (unsigned)((threads + 127) / 128); }
+
 int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, const int *nb_start,
-                   const int *nb_idx, int cap, int n, float sigma, float *rho_s, float *rho_out,
-                   float *h_next_out, float *mass_s, cudaStream_t st) {
+                   const int *nb_idx, int cap, int n, float sigma, int lanes, float *rho_s,
+                   float *rho_out, float *h_next_out, float *mass_s, cudaStream_t st) {
     if (n > 0) {
-        density_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, mass, perm, nb_start, nb_idx, cap,
-                                                        n, sigma, rho_s, rho_out, h_next_out, mass_s);
-        note_launch();
+        gather_mass_kernel<<<(n + 255) / 256, 256, 0, st>>>(mass, perm, n, mass_s);
+        const long long T = (long long)n * lanes;
+        switch (lanes) {
+            case 1: density_kernel<1><<<grid_for(T), 128, 0, st>>>(pos_h_s, mass_s, perm, nb_start, nb_idx, cap, n, sigma, rho_s, rho_out, h_next_out); break;
+            case 2: density_kernel<2><<<grid_for(T), 128, 0, st>>>(pos_h_s, mass_s, perm, nb_start, nb_idx, cap, n, sigma, rho_s, rho_out, h_next_out); break;
+            case 8: density_kernel<8><<<grid_for(T), 128, 0, st>>>(pos_h_s, mass_s, perm, nb_start, nb_idx, cap, n, sigma, rho_s, rho_out, h_next_out); break;
+            default: density_kernel<4><<<grid_for(T), 128, 0, st>>>(pos_h_s, mass_s, perm, nb_start, nb_idx, cap, n, sigma, rho_s, rho_out, h_next_out); break;
+        }
+        note_launch(2);
     }
     SPH_LAUNCH_CHECK();
     return SPH_OK;
@@ -231,10 +274,15 @@ int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, 
 
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp, float4 *acc_out, cudaStream_t st) {
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st) {
     if (n > 0) {
-        forces_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start,
-                                                       nb_idx, cap, n, hp, acc_out);
+        const long long T = (long long)n * lanes;
+        switch (lanes) {
+            case 1: forces_kernel<1><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
+            case 2: forces_kernel<2><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
+            case 8: forces_kernel<8><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
+            default: forces_kernel<4><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
+        }
         note_launch();
     }
     SPH_LAUNCH_CHECK();

@@ -57,8 +57,8 @@ struct HydroParams {
     float gamma, alpha, beta, eta, sigma;
 };
 int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, const int *nb_start,
-                   const int *nb_idx, int cap, int n, float sigma, float *rho_s, float *rho_out,
-                   float *h_next_out, float *mass_s, cudaStream_t st);
+                   const int *nb_idx, int cap, int n, float sigma, int lanes, float *rho_s,
+                   float *rho_out, float *h_next_out, float *mass_s, cudaStream_t st);
 int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
                       int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st);
 int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, const int *perm,
@@ -67,7 +67,6 @@ int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, 
                cudaStream_t st);
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp,
-                  float4 *acc_out, cudaStream_t st);
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st);
 
 }  // namespace sphgb

@@ -69,11 +69,31 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                     }
             if (!any) continue;
         }
-        for (int cz = lz; cz <= hz; ++cz)
-            for (int cy = ly; cy <= hy; ++cy)
+        // per-axis distance from the particle to each probed cell, widened by a
+        // margin that covers the rounding of the binning (a skipped cell cannot
+        // hold a particle within h_i + hmax of the cell's bucket)
+        const float csz = pow2f(g.log2_L0 + l);
+        // |coordinate| of anything in the box is at most |x0| + (hi + 1) csz
+        const float mx = 9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f;
+        const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
+        const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
+        for (int cz = lz; cz <= hz; ++cz) {
+            const float z0c = fmaf((float)cz, csz, g.z0);
+            const float dz = fmaxf(0.0f, fmaxf(z0c - p.z, p.z - (z0c + csz)) - mz);
+            for (int cy = ly; cy <= hy; ++cy) {
+                const float y0c = fmaf((float)cy, csz, g.y0);
+                const float dy = fmaxf(0.0f, fmaxf(y0c - p.y, p.y - (y0c + csz)) - my);
                 for (int cx = lx; cx <= hx; ++cx) {
+                    const float x0c = fmaf((float)cx, csz, g.x0);
+                    const float dx = fmaxf(0.0f, fmaxf(x0c - p.x, p.x - (x0c + csz)) - mx);
                     const int k = bucket_of(cx, cy, cz, l + kMaxLevels * si, g.log2_M);
                     const int s = a.cell_start[k], e = a.cell_start[k + 1];
+                    if (s == e) continue;
+                    {
+                        const float reach = p.w + __uint_as_float(a.hmax_cell[k]);
+                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (d2 > reach * reach * (1.0f + 3.0517578125e-05f)) continue;
+                    }
                     for (int j = s; j < e; ++j) {
                         if (j == i) continue;
                         if (a.sim_s && a.sim_s[j] != si) continue;
@@ -99,6 +119,8 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                         ++cnt;
                     }
                 }
+            }
+        }
     }
     if (!FILL) a.own[i] = cnt;
 }

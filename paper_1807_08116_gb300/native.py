@@ -113,6 +113,7 @@ def lib():
                                     ctypes.POINTER(_P)]),
             "sph_ctx_destroy": (_I, [_P]),
             "sph_ctx_set_params": (_I, [_P, ctypes.POINTER(SphParams)]),
+            "sph_ctx_set_lanes": (_I, [_P, _I]),
             "sph_ctx_device_status": (_I, [_P, _P, ctypes.POINTER(_I)]),
             "sph_ctx_get_grid": (_I, [_P, _P, ctypes.POINTER(SphGrid)]),
             "sph_ctx_nb_total": (_I, [_P, _P, ctypes.POINTER(_I64)]),
@@ -241,6 +242,11 @@ class Ctx:
             self.close()
         except Exception:
             pass
+
+    def set_lanes(self, lanes):
+        """Lanes per neighbour row in the density / force kernels (1, 2, 4, 8)."""
+        _check("sph_ctx_set_lanes", lib().sph_ctx_set_lanes(self.handle, int(lanes)))
+        self.lanes = int(lanes)
 
     def device_status(self, stream=None):
         f = _I()

@@ -69,6 +69,7 @@ class Simulation:
         self.grav_flags = int(grav_flags)
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)
         self.ctx = None
+        self.lanes = None
         self.nb_per_particle = nb_per_particle
         self.batch = None
         if batch_offsets is not None:
@@ -85,6 +86,8 @@ class Simulation:
     def _make_ctx(self, capacity):
         old = self.ctx
         self.ctx = nv.Ctx(max(1, self.n_gas), capacity, device=self.device, **self.params)
+        if self.lanes:
+            self.ctx.set_lanes(self.lanes)
         if self.batch is not None:
             nv.sph_ctx_set_batch(self.ctx, self.batch)
         if old is not None:
@@ -176,6 +179,11 @@ class Simulation:
         g0, g1 = int(self.gas_off[s]), int(self.gas_off[s + 1])
         d0, d1 = int(self.dark_off[s]), int(self.dark_off[s + 1])
         return np.concatenate([np.arange(g0, g1), self.n_gas + np.arange(d0, d1)])
+
+    def set_lanes(self, lanes):
+        """Lanes per neighbour row in the density / force kernels."""
+        self.lanes = int(lanes)
+        self.ctx.set_lanes(self.lanes)
 
     def cfl_dt(self, C=0.5):
         """Next time step from the modified CFL condition (Eq. 17) at the

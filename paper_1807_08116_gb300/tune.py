@@ -54,3 +54,17 @@ def tune_batch(batch, pos_m, G=1.0, eps=0.01, flags=0, reps=2):
     best = min(res, key=res.get)
     batch.set_plan(best)
     return best, res
+
+
+def tune_lanes(sim, reps=3):
+    """Time the force kernel of a Simulation (after its first evaluation) for
+    1, 2, 4 and 8 lanes per neighbour row; keep the fastest."""
+    t = sim.t
+    res = {}
+    for lanes in (1, 2, 4, 8):
+        sim.set_lanes(lanes)
+        res[lanes] = _time(lambda: nv.sph_forces(sim.ctx, t["vel_e"], t["rho"],
+                                                 t["mass"][:sim.n_gas], t["acc_hyd"]), reps)
+    best = min(res, key=res.get)
+    sim.set_lanes(best)
+    return best, res

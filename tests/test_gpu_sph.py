@@ -24,8 +24,9 @@ def _setup(ph, cap_per=200):
     return torch, nv, ctx
 
 
-def _density(ph, mass):
+def _density(ph, mass, lanes=4):
     torch, nv, ctx = _setup(ph)
+    ctx.set_lanes(lanes)
     n = len(ph)
     m = torch.as_tensor(mass, device="cuda")
     rho = torch.empty(n, device="cuda")
@@ -35,11 +36,12 @@ def _density(ph, mass):
     return ctx, rho.cpu().numpy(), hn.cpu().numpy()
 
 
-def _forces(ph, ve, mass, rho, **params):
+def _forces(ph, ve, mass, rho, lanes=4, **params):
     torch = need_gpu()
     from paper_1807_08116_gb300 import native as nv
     n = len(ph)
     ctx = nv.Ctx(n, max(1024, 200 * n), **params)
+    ctx.set_lanes(lanes)
     nv.sph_bin_and_sort(ctx, torch.as_tensor(ph, device="cuda"))
     nv.sph_build_neighbors(ctx, n)
     out = torch.full((n, 4), float("nan"), device="cuda")
@@ -70,10 +72,11 @@ def _stirred(d, seed=0):
     return ph, mass, ve
 
 
-def test_density_single_halo(orc):
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_density_single_halo(orc, lanes):
     d = ics.single_halo(8192, 8192, seed=0)
     ph, mass, _ = _gas(d)
-    _, rho, hn = _density(ph, mass)
+    _, rho, hn = _density(ph, mass, lanes)
     orho, ohn = orc.density(ph, mass)
     r1, m1 = err(rho, orho)
     r2, m2 = err(hn, ohn)
@@ -82,12 +85,13 @@ def test_density_single_halo(orc):
     assert r2 <= RHO_RMS and m2 <= RHO_MAX
 
 
-def test_forces_single_halo(orc):
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_forces_single_halo(orc, lanes):
     d = ics.single_halo(8192, 8192, seed=0)
     ph, mass, ve = _stirred(d)
     orho, _ = orc.density(ph, mass)
     rho = orho.astype(np.float32)
-    a = _forces(ph, ve, mass, rho)
+    a = _forces(ph, ve, mass, rho, lanes)
     oa, ode = orc.hydro(ph, ve, mass, rho)
     ra, ma = err(a[:, :3], oa)
     re, me = err(a[:, 3:], ode[:, None])
