@@ -339,8 +339,16 @@ extern "C" int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_st
     a.nb_idx = ctx->nb_idx;
     a.capacity = ctx->capacity;
     a.flags = ctx->flags;
+    // single search pass when the scratch array can stage >= 48 own entries
+    // per row; otherwise count and fill with two searches
+    const long long room = n > 0 ? std::max<long long>(ctx->capacity, n) / n : 0;
+    a.stage_k = (int)std::min<long long>(128, room & ~15ll);
+    a.stage = a.stage_k >= 48 ? ctx->tmp : nullptr;
+    a.list = ctx->long_list;
+    a.list_count = ctx->long_count;
     int rc;
     if (n > 0) SPH_CUDA_TRY(cudaMemsetAsync(ctx->rev, 0, sizeof(int) * (size_t)n, st));
+    if (a.stage) SPH_CUDA_TRY(cudaMemsetAsync(ctx->long_count, 0, sizeof(int), st));
     if ((rc = launch_nb_count(a, st))) return rc;
     if ((rc = launch_row_len(ctx->own, ctx->rev, n, ctx->row_len, st))) return rc;
     if ((rc = launch_scan_exclusive(ctx->row_len, n, ctx->nb_start, ctx->block_sums, st))) return rc;

@@ -44,11 +44,19 @@ namespace sphgb {
 #ifndef SPHGB_GR_MINB
 #define SPHGB_GR_MINB 2
 #endif
+#ifndef SPHGB_GR_NBUF
+#define SPHGB_GR_NBUF 2
+#endif
 
 constexpr int GR_THREADS = SPHGB_GR_THREADS;
 constexpr int GR_UNROLL = SPHGB_GR_UNROLL;
 constexpr int GR_TJ = SPHGB_GR_TJ;                 // sources per tile
-constexpr int GR_SMEM = 4 * GR_TJ * 16 + 64;       // two raw tiles, one expanded, mbarriers
+constexpr int GR_NBUF = SPHGB_GR_NBUF;             // raw tiles in flight (TMA ring)
+// raw ring + expanded tile + mbarriers; the cluster reduction reuses the same
+// space for 4 x (256 x 8) floats at most
+constexpr int GR_SMEM_TILES = (GR_NBUF + 2) * GR_TJ * 16;
+constexpr int GR_SMEM_RED = 4 * GR_THREADS * 8 * 4;
+constexpr int GR_SMEM = (GR_SMEM_TILES > GR_SMEM_RED ? GR_SMEM_TILES : GR_SMEM_RED) + 64;
 
 __device__ int g_grav_flags;
 
@@ -196,9 +204,9 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
                   float4 *__restrict__ out) {
     constexpr int R = 2 * RP;
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *tiles = reinterpret_cast<float4 *>(smem);            // [2][GR_TJ] raw
-    float4 *dup = tiles + 2 * GR_TJ;                              // [GR_TJ][2] expanded
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(dup + 2 * GR_TJ);
+    float4 *tiles = reinterpret_cast<float4 *>(smem);            // [GR_NBUF][GR_TJ] raw
+    float4 *dup = tiles + GR_NBUF * GR_TJ;                        // [GR_TJ][2] expanded
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + GR_SMEM - 64);
     const int tid = threadIdx.x;
     const int rank = blockIdx.x % S;   // cluster dims (S, 1, 1): rank == ctarank
     const int i0 = (blockIdx.x / S) * (GR_THREADS * R);
@@ -224,14 +232,13 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
     const unsigned bar0 = smem_u32(&bars[0]);
     const unsigned tiles0 = smem_u32(tiles);
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+        for (int b = 0; b < GR_NBUF; ++b) mbar_init(bar0 + 8 * b, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0) {
-        for (int b = 0; b < 2 && b < my_tiles; ++b) {
+        for (int b = 0; b < GR_NBUF && b < my_tiles; ++b) {
             int j0 = (t_begin + b) * GR_TJ;
             unsigned bytes = (unsigned)min(GR_TJ, n - j0) * 16u;
             mbar_expect_tx(bar0 + 8 * b, bytes);
@@ -242,16 +249,16 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
     const float2 e2 = make_float2(eps2, eps2);
     bool failed = false;
     for (int t = 0; t < my_tiles; ++t) {
-        const int buf = t & 1;
-        bool ok = mbar_wait_bounded(bar0 + 8 * buf, (unsigned)((t >> 1) & 1));
+        const int buf = t % GR_NBUF;
+        bool ok = mbar_wait_bounded(bar0 + 8 * buf, (unsigned)((t / GR_NBUF) & 1));
         if (__syncthreads_or(!ok)) { failed = true; break; }
         const int cnt = min(GR_TJ, n - (t_begin + t) * GR_TJ);
         const float4 *tb = tiles + buf * GR_TJ;
         expand_tile(tb, dup, cnt);
         __syncthreads();   // raw buffer consumed, expanded tile visible
-        if (tid == 0 && t + 2 < my_tiles) {
+        if (tid == 0 && t + GR_NBUF < my_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            int j0 = (t_begin + t + 2) * GR_TJ;
+            int j0 = (t_begin + t + GR_NBUF) * GR_TJ;
             unsigned bytes = (unsigned)min(GR_TJ, n - j0) * 16u;
             mbar_expect_tx(bar0 + 8 * buf, bytes);
             bulk_g2s(tiles0 + buf * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * buf);
@@ -333,14 +340,13 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_unit;
     float4 *tiles = reinterpret_cast<float4 *>(smem);
-    float4 *dup = tiles + 2 * GR_TJ;
-    unsigned long long *bars = reinterpret_cast<unsigned long long *>(dup + 2 * GR_TJ);
+    float4 *dup = tiles + GR_NBUF * GR_TJ;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + GR_SMEM - 64);
     const int tid = threadIdx.x;
     const unsigned bar0 = smem_u32(&bars[0]);
     const unsigned tiles0 = smem_u32(tiles);
     if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+        for (int b = 0; b < GR_NBUF; ++b) mbar_init(bar0 + 8 * b, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -375,12 +381,12 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
 #pragma unroll
         for (int k = 0; k < R; ++k) { ax[k].init(); ay[k].init(); az[k].init(); ph[k].init(); }
 
-        // land virtual source tile t into buffer (seq + t) & 1
+        // land virtual source tile t into buffer (seq + t) % GR_NBUF
         auto issue = [&](int t) {
             const int v0 = t * GR_TJ, v1 = min(ns, v0 + GR_TJ);
             const int gcnt = max(0, min(v1, ng) - v0);
             const int dcnt = (v1 - v0) - gcnt;
-            const unsigned buf = (seq + t) & 1u;
+            const unsigned buf = (seq + t) % GR_NBUF;
             const unsigned bar = bar0 + 8 * buf, dst = tiles0 + buf * GR_TJ * 16;
             mbar_expect_tx(bar, (unsigned)(v1 - v0) * 16u);
             if (gcnt) bulk_g2s(dst, pos + sr.x + v0, (unsigned)gcnt * 16u, bar);
@@ -388,19 +394,19 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
         };
         if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int b = 0; b < 2 && b < nt; ++b) issue(b);
+            for (int b = 0; b < GR_NBUF && b < nt; ++b) issue(b);
         }
         for (int t = 0; t < nt; ++t) {
             const unsigned q = seq + t;
-            const int buf = q & 1;
-            bool ok = mbar_wait_bounded(bar0 + 8 * buf, (q >> 1) & 1u);
+            const int buf = q % GR_NBUF;
+            bool ok = mbar_wait_bounded(bar0 + 8 * buf, (q / GR_NBUF) & 1u);
             if (__syncthreads_or(!ok)) { failed = true; break; }
             const int cnt = min(GR_TJ, ns - t * GR_TJ);
             expand_tile(tiles + buf * GR_TJ, dup, cnt);
             __syncthreads();
-            if (tid == 0 && t + 2 < nt) {
+            if (tid == 0 && t + GR_NBUF < nt) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(t + 2);
+                issue(t + GR_NBUF);
             }
             float2 sx[RP], sy[RP], sz[RP], sp[RP];
             tile_sums<RP, POT, GUARD>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp);

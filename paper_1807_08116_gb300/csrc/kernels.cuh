@@ -47,6 +47,10 @@ struct NbArgs {
     int *nb_idx;
     long long capacity;
     int *flags;
+    int *stage;              // [n * stage_k] own entries of the single-search build, or NULL
+    int stage_k;
+    int *list;               // rows whose own part exceeds stage_k
+    int *list_count;
 };
 int launch_nb_count(const NbArgs &a, cudaStream_t st);
 int launch_nb_fill(const NbArgs &a, cudaStream_t st);

@@ -32,9 +32,31 @@ __device__ __forceinline__ void search_box(float x, float R, float x0, float inv
     hi = cell_of(__fadd_rn(x, m), x0, inv_c);
 }
 
-template <bool FILL>
+// Distance from coordinate x to cell c of size csz (origin x0), less a
+// rounding margin m; the end cells also hold everything clamped into them,
+// so they are open on their outer side.
+__device__ __forceinline__ float cell_gap(float x, int c, float csz, float x0, float m) {
+    const float lo = fmaf((float)c, csz, x0);
+    const float below = c > 0 ? lo - x : -1.0f;
+    const float above = c < kCellMax ? x - (lo + csz) : -1.0f;
+    return fmaxf(0.0f, fmaxf(below, above) - m);
+}
+
+// MODE: NB_COUNT counts own entries (and reverse entries of the coarser
+// partners); NB_FILL writes own and reverse entries into their CSR places;
+// NB_STAGE counts like NB_COUNT and also writes the first stage_k own
+// entries of the row to stage[i * stage_k + c] (rows with more are queued on
+// the overflow list); NB_FILL_LISTED runs NB_FILL for the queued rows only.
+enum { NB_COUNT = 0, NB_FILL = 1, NB_STAGE = 2, NB_FILL_LISTED = 3 };
+
+template <int MODE>
 __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (MODE == NB_FILL_LISTED) {
+        if (i >= *a.list_count) return;
+        i = a.list[i];
+    }
     if (i >= a.n) return;
     const GridDev g = *a.grid;
     const float4 p = a.pos_h_s[i];
@@ -78,14 +100,11 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
         const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
         const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
         for (int cz = lz; cz <= hz; ++cz) {
-            const float z0c = fmaf((float)cz, csz, g.z0);
-            const float dz = fmaxf(0.0f, fmaxf(z0c - p.z, p.z - (z0c + csz)) - mz);
+            const float dz = cell_gap(p.z, cz, csz, g.z0, mz);
             for (int cy = ly; cy <= hy; ++cy) {
-                const float y0c = fmaf((float)cy, csz, g.y0);
-                const float dy = fmaxf(0.0f, fmaxf(y0c - p.y, p.y - (y0c + csz)) - my);
+                const float dy = cell_gap(p.y, cy, csz, g.y0, my);
                 for (int cx = lx; cx <= hx; ++cx) {
-                    const float x0c = fmaf((float)cx, csz, g.x0);
-                    const float dx = fmaxf(0.0f, fmaxf(x0c - p.x, p.x - (x0c + csz)) - mx);
+                    const float dx = cell_gap(p.x, cx, csz, g.x0, mx);
                     const int k = bucket_of(cx, cy, cz, l + kMaxLevels * si, g.log2_M);
                     const int s = a.cell_start[k], e = a.cell_start[k + 1];
                     if (s == e) continue;
@@ -113,8 +132,10 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                                 if (wr < a.capacity) a.nb_idx[wr] = i;
                                 else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
                             }
-                        } else if (l > li) {
-                            atomicAdd(&a.rev[j], 1);
+                        } else {
+                            if (MODE == NB_STAGE && cnt < a.stage_k)
+                                a.stage[(long long)i * a.stage_k + cnt] = j;
+                            if (l > li) atomicAdd(&a.rev[j], 1);
                         }
                         ++cnt;
                     }
@@ -123,6 +144,33 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
         }
     }
     if (!FILL) a.own[i] = cnt;
+    if (MODE == NB_STAGE && cnt > a.stage_k) a.list[atomicAdd(a.list_count, 1)] = i;
+}
+
+// Second half of the single-search build: copy each staged row into its CSR
+// place and append the row to the reverse part of every coarser partner
+// (rows on the overflow list are filled by NB_FILL_LISTED instead).
+__global__ void __launch_bounds__(128) nb_copy_kernel(NbArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int cnt = a.own[i];
+    if (cnt > a.stage_k) return;
+    const GridDev g = *a.grid;
+    const int li = level_of(a.pos_h_s[i].w, g.log2_L0, g.n_levels);
+    const long long base = a.nb_start[i];
+    const int *row = a.stage + (long long)i * a.stage_k;
+    for (int c = 0; c < cnt; ++c) {
+        const int j = row[c];
+        const long long w = base + c;
+        if (w < a.capacity) a.nb_idx[w] = j;
+        else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+        if (level_of(a.pos_h_s[j].w, g.log2_L0, g.n_levels) > li) {
+            const int pos = atomicAdd(&a.rev[j], 1);
+            const long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
+            if (wr < a.capacity) a.nb_idx[wr] = i;
+            else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+        }
+    }
 }
 
 __global__ void row_len_kernel(const int *__restrict__ own, const int *__restrict__ rev, int n,
@@ -133,7 +181,8 @@ __global__ void row_len_kernel(const int *__restrict__ own, const int *__restric
 
 int launch_nb_count(const NbArgs &a, cudaStream_t st) {
     if (a.n > 0) {
-        nb_kernel<false><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+        if (a.stage) nb_kernel<NB_STAGE><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+        else nb_kernel<NB_COUNT><<<(a.n + 127) / 128, 128, 0, st>>>(a);
         note_launch();
     }
     SPH_LAUNCH_CHECK();
@@ -142,8 +191,14 @@ int launch_nb_count(const NbArgs &a, cudaStream_t st) {
 
 int launch_nb_fill(const NbArgs &a, cudaStream_t st) {
     if (a.n > 0) {
-        nb_kernel<true><<<(a.n + 127) / 128, 128, 0, st>>>(a);
-        note_launch();
+        if (a.stage) {
+            nb_copy_kernel<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+            nb_kernel<NB_FILL_LISTED><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+            note_launch(2);
+        } else {
+            nb_kernel<NB_FILL><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+            note_launch();
+        }
     }
     SPH_LAUNCH_CHECK();
     return SPH_OK;
