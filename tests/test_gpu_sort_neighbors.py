@@ -247,3 +247,19 @@ def test_giant_reverse_segments(orc):
     _sort(ph, ctx=ctx2)
     s2, i2 = _lists(ctx2, n)
     assert np.array_equal(s2, start) and np.array_equal(i2, idx)
+
+
+def test_two_pass_fallback_when_scratch_is_small(orc):
+    # sparse neighbourhoods and a capacity below 48 entries per row: the build
+    # falls back to the count + fill searches; the lists are the same
+    rng = np.random.default_rng(61)
+    n = 3000
+    ph = pos_h_of(rng.uniform(0, 1, size=(n, 3)), np.full(n, 0.03))
+    small = _ctx(n, cap=40 * n)
+    big = _ctx(n, cap=200 * n)
+    _, _, _, perm = _sort(ph, ctx=small)
+    a = _lists(small, n)
+    _sort(ph, ctx=big)
+    b = _lists(big, n)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    _check_lists(orc, ph, small, perm, rows=np.arange(0, n, 7))
