@@ -46,8 +46,8 @@ WORKLOAD_NAMES = {
 # DRAM bytes (read + write) of one gravity launch on the large two-halo
 # workload, from an ncu capture of the kernel source with this SHA-256 (the
 # figure is reported only while csrc/gravity.cu is unchanged).
-GFC_TRAFFIC = {"sha256": "c160e99ba84dba7cf59f2c438ad75d19576864efecca6d0b02b07c39621a64f0",
-               "bytes": 855.29e6, "n": 4194304}
+GFC_TRAFFIC = {"sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721",
+               "bytes": 870.39e6, "n": 4194304}
 # FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
