@@ -314,6 +314,15 @@ def run_ours(args):
         v, t_step, threads, desc = oracle_sample(ic, args.cpu_rows, args.cpu_rows)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
                "sample": desc}
+        # the same oracle on one host thread, on a sample 1/16 the size
+        import oracle
+        oracle.set_threads(1)
+        try:
+            rows1 = max(64, args.cpu_rows // 16)
+            v1, _, threads1, desc1 = oracle_sample(ic, rows1, rows1, seed=1)
+        finally:
+            oracle.set_threads(threads)
+        cpu["single_thread"] = {"value": v1, "cores": threads1, "sample": desc1}
 
     if rank == 0:
         line = {

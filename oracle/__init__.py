@@ -62,6 +62,8 @@ def _load():
             D = ctypes.c_double
             lib.oracle_threads.restype = I
             lib.oracle_threads.argtypes = []
+            lib.oracle_set_threads.restype = I
+            lib.oracle_set_threads.argtypes = [I]
             lib.oracle_W.restype = D
             lib.oracle_W.argtypes = [D, D]
             lib.oracle_Wp.restype = D
@@ -104,6 +106,11 @@ def _rows(rows, n):
 def threads() -> int:
     """Number of host threads the oracle's parallel loops use."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """Use n host threads in the parallel loops; returns the count in effect."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 # -- kernels (Eqs. 8, 9) ------------------------------------------------------

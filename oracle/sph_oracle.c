@@ -59,6 +59,18 @@ int oracle_threads(void)
 #endif
 }
 
+/* Set the thread count of the parallel loops (n >= 1; no effect without
+ * OpenMP).  Returns the count now in effect. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return oracle_threads();
+}
+
 /* ------------------------------------------------------------------------ */
 /* Smoothing kernels, Eqs. 8 and 9.                                         */
 /* ------------------------------------------------------------------------ */

@@ -98,3 +98,20 @@ def test_two_body_circular_orbit(orc):
     # second-order scheme (Sect. 2.2): halving dt divides the phase error by 4
     assert errs[1] < 3e-5
     assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_thread_count_does_not_change_results(orc):
+    # each target row is summed by one thread in source order, so the
+    # single-thread timing row of the bench measures the same arithmetic
+    d = ics.single_halo(300, 300, seed=9)
+    pm = _pos_m(d["r"], d["m"])
+    n0 = orc.threads()
+    try:
+        orc.set_threads(1)
+        assert orc.threads() == 1
+        a1, p1 = orc.gravity(pm, G=1.0, eps=0.01)
+        orc.set_threads(max(2, n0))
+        a2, p2 = orc.gravity(pm, G=1.0, eps=0.01)
+    finally:
+        orc.set_threads(n0)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
