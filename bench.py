@@ -44,10 +44,14 @@ WORKLOAD_NAMES = {
     "single": "single Plummer halo 8192 gas + 8192 dark",
 }
 # DRAM bytes (read + write) of one gravity launch on the large two-halo
-# workload, from an ncu capture of the kernel source with this SHA-256 (the
-# figure is reported only while csrc/gravity.cu is unchanged).
-GFC_TRAFFIC = {"sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721",
-               "bytes": 870.39e6, "n": 4194304}
+# workload, per kernel source, from an ncu capture of the source file with
+# this SHA-256 (a figure is reported only while that file is unchanged).
+GFC_TRAFFIC = {
+    "pp_gravity_kernel": {"file": "gravity.cu", "n": 4194304, "bytes": 870.39e6,
+                          "sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721"},
+    "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": None,
+                                "sha256": None},
+}
 # FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
@@ -69,17 +73,26 @@ def aggregate_rate(world, n, steps, ms):
     return world * n * steps / (ms / 1e3)
 
 
-def gfc_traffic(n):
-    """Per-launch DRAM bytes of the gravity kernel if the capture applies."""
+def gfc_traffic(n, kernel="pp_gravity_kernel"):
+    """Per-launch DRAM bytes of a gravity kernel if its capture applies."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1807_08116_gb300", "csrc", "gravity.cu")
+    rec = GFC_TRAFFIC.get(kernel)
+    if rec is None or rec["bytes"] is None or n != rec["n"]:
+        return None
+    src = os.path.join(ROOT, "paper_1807_08116_gb300", "csrc", rec["file"])
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    if digest != GFC_TRAFFIC["sha256"] or n != GFC_TRAFFIC["n"]:
-        return None
-    return GFC_TRAFFIC["bytes"]
+    return rec["bytes"] if digest == rec["sha256"] else None
+
+
+# FP32-pipe operations per ordered interaction: the one-sided kernel does
+# 3 FADD + 3 FFMA + 3 FMUL + 3 FFMA (+1 MUFU); the pair-once kernel does 16
+# per unordered pair (3 FADD, 3 FFMA, 4 FMUL, 2 x 3 FFMA), i.e. 8 per
+# ordered interaction.
+FP32_OPS = {"pp_gravity_kernel": 12, "pp_gravity_pairs_kernel": 8}
+FP32_LANE_OPS_PER_S = 152 * 128 * 2.07e9
 
 
 def make_ic(name, rank=0):
@@ -300,14 +313,25 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (gravity) -------------------------
     gfc_ms = stage["gfc"]
     achieved = FLOP_PER_INTERACTION * float(n) * float(n) / (gfc_ms / 1e3) / 1e12
-    R, S = nv.sph_gravity_plan(n)
+    ips = float(n) * n / (gfc_ms / 1e3)
+    if "grav_work" in sim.t and nv.pp_gravity_pairs_eligible(n, sim.params["eps"], sim.grav_flags):
+        kernel = "pp_gravity_pairs_kernel"
+        plan = {"scheme": "each unordered pair once (Newton's third law)", "block": 2048,
+                "targets_per_thread": 8}
+    else:
+        kernel = "pp_gravity_kernel"
+        R, S = nv.sph_gravity_plan(n)
+        plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": args.gfc_traffic if args.gfc_traffic is not None else gfc_traffic(n),
-            "kernel": "pp_gravity_kernel", "interactions_per_s": float(n) * n / (gfc_ms / 1e3),
+            "traffic": args.gfc_traffic if args.gfc_traffic is not None else gfc_traffic(n, kernel),
+            "kernel": kernel, "interactions_per_s": ips,
             "flop_per_interaction": FLOP_PER_INTERACTION,
-            "peak_note": "FP32 pipe 152 SM x 128 lanes x 2 flop x 2.07 GHz (derived, not measured)",
-            "plan": {"targets_per_thread": R, "cluster_split": S}}
+            "fp32_ops_per_interaction": FP32_OPS[kernel],
+            "fp32_pipe_frac": FP32_OPS[kernel] * ips / FP32_LANE_OPS_PER_S,
+            "peak_note": "FP32 pipe 152 SM x 128 lanes x 2 flop x 2.07 GHz (derived, not measured); "
+                         "achieved counts 20 flop per ordered interaction (N^2 per evaluation)",
+            "plan": plan}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -529,26 +553,40 @@ def run_gravity(args):
     pm[:, 3] = d["m"]
     x = torch.as_tensor(pm, device="cuda")
     out = torch.empty_like(x)
+    n = d["n"]
+    pairs = not args.one_sided and nv.pp_gravity_pairs_eligible(n, 0.01)
+    work = nv.pp_gravity_pairs_workspace(n) if pairs else None
+
+    def launch():
+        if pairs:
+            nv.pp_gravity_pairs(x, out, work)
+        else:
+            nv.pp_gravity(x, out)
     for _ in range(args.warmup):
-        nv.pp_gravity(x, out)
+        launch()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        nv.pp_gravity(x, out)
+        launch()
     e1.record()
     torch.cuda.synchronize()
     if nv.pp_gravity_status():
         raise RuntimeError("gravity kernel reported a timeout")
     ms = e0.elapsed_time(e1) / args.steps
-    n = d["n"]
     ips = float(n) * n / (ms / 1e3)
-    R, S = nv.sph_gravity_plan(n)
+    kernel = "pp_gravity_pairs_kernel" if pairs else "pp_gravity_kernel"
+    if pairs:
+        plan = {"scheme": "each unordered pair once", "block": 2048, "targets_per_thread": 8}
+    else:
+        R, S = nv.sph_gravity_plan(n)
+        plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
     print(json.dumps({"metric": "PP interactions/s", "value": ips, "unit": "interactions/s",
                       "n": n, "ms_per_launch": ms, "steps": args.steps, "warmup": args.warmup,
-                      "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12,
+                      "kernel": kernel, "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12,
                       "frac_of_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / FP32_PEAK_TFLOPS,
-                      "plan": {"targets_per_thread": R, "cluster_split": S}}), flush=True)
+                      "fp32_pipe_frac": FP32_OPS[kernel] * ips / FP32_LANE_OPS_PER_S,
+                      "plan": plan}), flush=True)
     return 0
 
 
@@ -561,6 +599,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "gravity"],
                     default="large")
     ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity")
+    ap.add_argument("--one-sided", action="store_true",
+                    help="--workload gravity: time the one-sided kernel instead of the pair-once one")
     ap.add_argument("--n-sims", type=int, default=64)
     ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--serve-window", type=float, default=90.0)

@@ -49,6 +49,7 @@ typedef struct CUstream_st *sph_stream_t;
 #define SPH_FLAG_SEARCH_WIDE   2   /* a search box exceeded 2^24 cells and was skipped */
 #define SPH_FLAG_TIMEOUT       4   /* a bounded mbarrier wait gave up */
 #define SPH_FLAG_ROW_UNSORTED  8   /* a segment too long to canonicalise was left as is */
+#define SPH_FLAG_GRAV_RANGE   16   /* pp_gravity_pairs: masses / eps put its fixed-point scale out of range */
 
 /* Model constants (Sect. 2): gravitational constant G and softening length
  * eps of Eq. 4 (Plummer form, |dr|^2 + eps^2); adiabatic index gamma of
@@ -249,6 +250,33 @@ int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t *h_S);
  * tiles); R = 0 returns to the built-in cost model. */
 int sph_gravity_tune(int32_t R, int32_t S);
 
+/* The same g_i (and phi_i) as pp_gravity with every unordered pair evaluated
+ * once (Newton's third law: one inverse cube serves both bodies, 16 instead
+ * of 2 x 12 FP32 operations per pair).  Bodies are cut into blocks of 2048;
+ * each tile of block pairs (I <= J) is one CTA, and the per-tile partial
+ * sums are accumulated exactly as 64-bit fixed-point integers whose scale is
+ * set per launch from sum |m_j| and eps, so the result is bitwise
+ * reproducible whatever the order the tiles run in.
+ * d_work (256-byte aligned, >= pp_gravity_pairs_workspace_bytes(n) bytes) is
+ * caller-owned scratch, overwritten.  Runs pp_gravity instead when the call
+ * is not eligible (pp_gravity_pairs_eligible) or the scratch is missing or
+ * too small.  SPH_FLAG_GRAV_RANGE in the status word: the masses or eps put
+ * the fixed-point scale outside 2^-250..2^250. */
+int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
+                     int32_t flags, void *d_work, size_t work_bytes, sph_stream_t stream);
+
+/* Scratch bytes of pp_gravity_pairs for n bodies (4096 + 32 n). */
+size_t pp_gravity_pairs_workspace_bytes(int32_t n);
+
+/* 1 if pp_gravity_pairs would use the pair-once kernel for n bodies: eps^2 > 0
+ * in FP32, no SPH_GRAV_NO_KAHAN, no plan fixed by sph_gravity_tune, and
+ * n >= the threshold of pp_gravity_pairs_min_n (default 65536). */
+int pp_gravity_pairs_eligible(int32_t n, float eps, int32_t flags);
+
+/* Set the smallest n for which pp_gravity_pairs uses the pair-once kernel
+ * (process-wide; 0 restores the default 65536). */
+int pp_gravity_pairs_min_n(int32_t n_min);
+
 /* Synchronise `stream`, read and clear the gravity kernel's device status
  * word (SPH_FLAG_TIMEOUT).  Returns SPH_ERR_DEVICE if a bit was set. */
 int pp_gravity_status(sph_stream_t stream, int32_t *h_flags);
@@ -297,6 +325,8 @@ typedef struct SphState {
     int32_t fresh;                /* 1 after sph_rhs_initial: the next step reuses its RHS */
     int32_t grav_flags;           /* flags passed to pp_gravity */
     void **events;                /* NULL, or 2 * SPH_NUM_STAGES cudaEvent_t (see sph_step) */
+    void *grav_work;              /* NULL, or scratch of pp_gravity_pairs for n bodies ... */
+    size_t grav_work_bytes;       /* ... of this many bytes (then gravity uses it) */
 } SphState;
 
 /* Stages of one sph_step, in launch order. */

@@ -459,6 +459,9 @@ int gravity_of(sph_ctx *ctx, SphState *s, sph_stream_t stream) {
         if (ctx->batch->n != s->n || ctx->batch->n_gas != s->n_gas) return SPH_ERR_INVALID_ARG;
         return pp_gravity_batched(ctx->batch, s->pos_m, G, eps, s->grav, s->grav_flags, stream);
     }
+    if (s->grav_work)
+        return pp_gravity_pairs(s->pos_m, s->n, G, eps, s->grav, s->grav_flags, s->grav_work,
+                                s->grav_work_bytes, stream);
     return pp_gravity(s->pos_m, s->n, G, eps, s->grav, s->grav_flags, stream);
 }
 

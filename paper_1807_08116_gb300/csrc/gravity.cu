@@ -24,7 +24,9 @@
 #include <mutex>
 #include <tuple>
 
+#include "async.cuh"
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -60,62 +62,6 @@ constexpr int GR_SMEM = (GR_SMEM_TILES > GR_SMEM_RED ? GR_SMEM_TILES : GR_SMEM_R
 
 __device__ int g_grav_flags;
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of an mbarrier, giving up after ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    unsigned long long t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes,
-                                         unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ float rsqrt_mufu(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // Expand a landed tile (x, y, z, m) into duplicated pairs ((x, x, y, y),
 // (z, z, m, m)), one per source.
 __device__ __forceinline__ void expand_tile(const float4 *__restrict__ tb, float4 *__restrict__ dup,
@@ -129,11 +75,15 @@ __device__ __forceinline__ void expand_tile(const float4 *__restrict__ tb, float
 
 // Sums of one tile for RP target pairs: 3 FADD2, 3 FFMA2, 2 MUFU.RSQ,
 // 3 FMUL2, 3 FFMA2 (+1 FADD2 for the potential) per source and pair.
-template <int RP, bool POT, bool GUARD>
+// SELF: the tile holds some of this CTA's own targets; source j of the tile
+// is target k of this thread when j == self_off + tid + k 256, and that term
+// is left out of the potential (its acceleration term is 0: dr = 0).
+template <int RP, bool POT, bool GUARD, bool SELF>
 __device__ __forceinline__ void tile_sums(const float4 *__restrict__ dup, int cnt,
                                           const float2 (&nx)[RP], const float2 (&ny)[RP],
                                           const float2 (&nz)[RP], float2 e2, float2 (&sx)[RP],
-                                          float2 (&sy)[RP], float2 (&sz)[RP], float2 (&sp)[RP]) {
+                                          float2 (&sy)[RP], float2 (&sz)[RP], float2 (&sp)[RP],
+                                          int self_off) {
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
         sx[p] = make_float2(0.f, 0.f); sy[p] = sx[p]; sz[p] = sx[p]; sp[p] = sx[p];
@@ -156,6 +106,11 @@ __device__ __forceinline__ void tile_sums(const float4 *__restrict__ dup, int cn
             if (GUARD) {
                 inv.x = r2.x > 0.f ? inv.x : 0.f;
                 inv.y = r2.y > 0.f ? inv.y : 0.f;
+            }
+            if (SELF) {
+                const int k0 = self_off + (int)threadIdx.x + (2 * p) * GR_THREADS;
+                if (j == k0) inv.x = 0.f;
+                if (j == k0 + GR_THREADS) inv.y = 0.f;
             }
             const float2 s = __fmul2_rn(qm, inv);
             // m / r^3 with two more FMUL2: a second MUFU op (1 / r^2) instead
@@ -264,22 +219,22 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
             bulk_g2s(tiles0 + buf * GR_TJ * 16, pos + j0, bytes, bar0 + 8 * buf);
         }
         float2 sx[RP], sy[RP], sz[RP], sp[RP];
-        tile_sums<RP, POT, GUARD>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp);
+        const int j0 = (t_begin + t) * GR_TJ;
+        if (POT && !GUARD && j0 < i0 + GR_THREADS * R && i0 < j0 + cnt)
+            tile_sums<RP, POT, GUARD, true>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp, i0 - j0);
+        else
+            tile_sums<RP, POT, GUARD, false>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp, 0);
         fold_tile<RP, POT, KAHAN>(ax, ay, az, ph, sx, sy, sz, sp);
         __syncthreads();   // expanded tile fully read before the next expansion
     }
     if (failed && tid == 0) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
-
-    // self term of the potential: the loop included j == i with |dr| = 0
-    const float self_inv = GUARD ? 0.f : rsqrt_mufu(eps2);
 
     if (S == 1) {
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             int i = i0 + tid + k * GR_THREADS;
             if (i < n) {
-                float m_i = pos[i].w;
-                float pot = POT ? -G * ((ph[k].s - ph[k].c) - m_i * self_inv) : 0.f;
+                float pot = POT ? -G * (ph[k].s - ph[k].c) : 0.f;
                 out[i] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
                                      G * (az[k].s - az[k].c), pot);
             }
@@ -313,10 +268,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
             a3 += peer[3 * NB + q];
         }
         int i = i0 + q;
-        if (i < n) {
-            float m_i = pos[i].w;
-            out[i] = make_float4(G * a0, G * a1, G * a2, POT ? -G * (a3 - m_i * self_inv) : 0.f);
-        }
+        if (i < n) out[i] = make_float4(G * a0, G * a1, G * a2, POT ? -G * a3 : 0.f);
     }
     cluster.sync();
 }
@@ -351,7 +303,6 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     const float2 e2 = make_float2(eps2, eps2);
-    const float self_inv = GUARD ? 0.f : rsqrt_mufu(eps2);
     unsigned seq = 0;   // tiles this CTA has landed so far (mbarrier phases)
     bool failed = false;
     for (;;) {
@@ -409,7 +360,11 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
                 issue(t + GR_NBUF);
             }
             float2 sx[RP], sy[RP], sz[RP], sp[RP];
-            tile_sums<RP, POT, GUARD>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp);
+            const int v0 = t * GR_TJ;   // virtual index of the tile's first source
+            if (POT && !GUARD && v0 < vt0 + GR_THREADS * R && vt0 < v0 + cnt)
+                tile_sums<RP, POT, GUARD, true>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp, vt0 - v0);
+            else
+                tile_sums<RP, POT, GUARD, false>(dup, cnt, nx, ny, nz, e2, sx, sy, sz, sp, 0);
             fold_tile<RP, POT, KAHAN>(ax, ay, az, ph, sx, sy, sz, sp);
             __syncthreads();
         }
@@ -420,8 +375,7 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
             const int v = vt0 + tid + k * GR_THREADS;
             if (v < ns) {
                 const int i = v < ng ? sr.x + v : sr.z + (v - ng);
-                const float m_i = pos[i].w;
-                const float pot = POT ? -G * ((ph[k].s - ph[k].c) - m_i * self_inv) : 0.f;
+                const float pot = POT ? -G * (ph[k].s - ph[k].c) : 0.f;
                 out[i] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
                                      G * (az[k].s - az[k].c), pot);
             }
@@ -615,6 +569,23 @@ int gravity_num_sms() {
     std::call_once(g_grav_once, grav_init);
     return g_num_sms;
 }
+
+int *gravity_flags_device() {
+    constexpr int kMaxDevices = 64;
+    static int *ptr[kMaxDevices];
+    static std::mutex m;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(m);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_grav_flags) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<int *>(p);
+    }
+    return ptr[dev];
+}
+
+bool gravity_plan_forced() { return g_force_R.load() != 0; }
 
 int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *units, int n_units,
                            int *counter, int R, float G, float eps, float4 *out, int flags,

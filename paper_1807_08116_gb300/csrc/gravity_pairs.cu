@@ -1,0 +1,400 @@
+// gravity_pairs.cu -- direct particle-particle gravity (GFC, Eq. 4, Plummer-
+// softened reading) with every unordered pair evaluated once.
+//
+// The force of a pair is equal and opposite (Newton's third law), and the
+// softened kernel is symmetric, so one evaluation of
+//     inv = (|r_j - r_i|^2 + eps^2)^(-1/2),  w = inv^3
+// serves both bodies: g_i += m_j w (r_j - r_i) and g_j -= m_i w (r_j - r_i).
+// Per pair that is 16 FP32-pipe operations instead of 2 x 12 for the two
+// one-sided interactions.
+//
+// Layout of the work:
+//  * bodies are cut into blocks of B = 2048 (256 threads x 8 targets); the
+//    block pairs (I <= J) of the triangle are the tiles, one CTA each.  A
+//    diagonal tile (I, I) is evaluated one-sided (every target against every
+//    source of the block, j = i left out of the potential); an off-diagonal
+//    tile evaluates each of its B x B pairs once.
+//  * a CTA keeps its 2048 targets (block I) in registers, two per packed
+//    FP32x2 operation, and its 2048 sources (block J) in shared memory,
+//    expanded to (x, x, y, y), (z, z, m, m) so that each operand of a packed
+//    operation comes from one 16-byte load.
+//  * inside a warp, the 32 lanes hold different targets; in step t lane l
+//    takes source (l + t) mod 32 of a 32-source chunk, and the partial sum
+//    of source s moves one lane down per step (one shuffle), so after 32
+//    steps lane s holds the warp's sum for source s.  The warps' sums of a
+//    256-source slab are then added in a fixed order through shared memory.
+//  * each tile's partial sums (FP32, for its targets and for its sources)
+//    are converted to 64-bit fixed-point integers and added with integer
+//    atomics.  Integer addition is exact and associative, so the result does
+//    not depend on the order in which the CTAs run: it is bitwise
+//    reproducible.  The scale is fixed per launch from a bound on |g|:
+//    sum_j |m_j| max_r r / (r^2 + eps^2)^(3/2) = sum_j |m_j| 2 / (3 sqrt(3)
+//    eps^2), computed on the device in FP64 by a fixed-order reduction, and
+//    placed 2^61 below the int64 limit.  Values below 2^-61 of that bound are
+//    rounded away (an absolute error far below the FP32 rounding of any
+//    acceleration that is not ~10^10 times smaller than the largest possible
+//    one).
+//  * keeping the CTA this simple matters: a persistent form (work units of
+//    several tiles, TMA-staged source blocks, target sums kept across tiles)
+//    was measured 30% slower -- its loop nest made the compiler add register
+//    moves in the innermost loop (+21 ALU and +11 FMA-pipe instructions per
+//    32-pair step).
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "async.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sphgb {
+
+constexpr int GP_THREADS = 256;
+constexpr int GP_RP = 4;                      // target pairs per thread
+constexpr int GP_R = 2 * GP_RP;               // targets per thread
+constexpr int GP_B = GP_THREADS * GP_R;       // bodies per block
+constexpr int GP_WARPS = GP_THREADS / 32;
+constexpr int GP_SLAB = 256;                  // sources per cross-warp reduction
+constexpr int GP_MASS_BLOCKS = 256;
+constexpr int GP_SMEM_DUP = 2 * GP_B * 16;                  // (x, x, y, y), (z, z, m, m)
+constexpr int GP_SMEM_PART = GP_WARPS * GP_SLAB * 4 * 4;    // warp sums of a slab
+constexpr int GP_SMEM = GP_SMEM_DUP + GP_SMEM_PART;
+static_assert(GP_SMEM <= 227 * 1024, "shared memory of the pair kernel");
+static_assert(GP_B % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
+
+// Start of the workspace; the fixed-point sums follow at kPairsAccOffset.
+struct PairsHeader {
+    int status;           // 1: the scale could not be placed (masses / eps out of range)
+    int pad0;
+    float s_acc1, s_acc2; // 2^-e_acc as two float factors
+    float s_pot1, s_pot2; // 2^-e_pot
+    double lsb_acc, lsb_pot;
+    double mass_part[GP_MASS_BLOCKS];
+};
+constexpr size_t kPairsAccOffset = 4096;
+static_assert(sizeof(PairsHeader) <= kPairsAccOffset, "pairs header");
+
+// Tile b of the triangle -> (I, J), I <= J: tiles are numbered by J, then I
+// (b = J (J + 1) / 2 + I), so CTAs that run together share a source block.
+__device__ __forceinline__ void tile_of(long long b, int &I, int &J) {
+    int j = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)j * (j + 1) / 2 > b) --j;
+    while ((long long)(j + 1) * (j + 2) / 2 <= b) ++j;
+    J = j;
+    I = (int)(b - (long long)j * (j + 1) / 2);
+}
+
+// ---------------------------------------------------------------------------
+// Scale of the fixed-point sums.
+// ---------------------------------------------------------------------------
+__global__ void pairs_mass_kernel(const float4 *__restrict__ pos, int n, PairsHeader *__restrict__ h) {
+    __shared__ double s[256];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int lo = (int)((long long)n * b / GP_MASS_BLOCKS);
+    const int hi = (int)((long long)n * (b + 1) / GP_MASS_BLOCKS);
+    double v = 0.0;
+    for (int i = lo + tid; i < hi; i += 256) v += fabs((double)pos[i].w);
+    s[tid] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) s[tid] += s[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) h->mass_part[b] = s[0];
+}
+
+// Power-of-two scale 2^-e with the bound below 2^(e + 61), as two float
+// factors (each within the normal range for |e| <= 250) and as a double.
+__device__ void place_scale(double bound, float &s1, float &s2, double &lsb, int &status) {
+    int e = 0;
+    if (bound > 0.0 && bound <= 1.0e300) {
+        int k;
+        frexp(bound, &k);   // bound < 2^k
+        e = k - 61;
+    } else if (!(bound == 0.0)) {
+        status = 1;
+    }
+    if (e < -250 || e > 250) {
+        status = 1;
+        e = 0;
+    }
+    const int e1 = -e / 2, e2 = -e - e1;
+    s1 = ldexpf(1.0f, e1);
+    s2 = ldexpf(1.0f, e2);
+    lsb = ldexp(1.0, e);
+}
+
+__global__ void pairs_scale_kernel(float eps, PairsHeader *__restrict__ h) {
+    __shared__ double s[GP_MASS_BLOCKS];
+    const int tid = threadIdx.x;
+    s[tid] = h->mass_part[tid];
+    __syncthreads();
+    for (int w = GP_MASS_BLOCKS / 2; w > 0; w >>= 1) {
+        if (tid < w) s[tid] += s[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double M = s[0], e = (double)eps;
+        int status = 0;
+        // max over r of r / (r^2 + eps^2)^(3/2) is 2 / (3 sqrt 3 eps^2) < 0.385 / eps^2
+        place_scale(0.385 * M / (e * e), h->s_acc1, h->s_acc2, h->lsb_acc, status);
+        place_scale(M / e, h->s_pot1, h->s_pot2, h->lsb_pot, status);
+        h->status = status;
+    }
+}
+
+__device__ __forceinline__ unsigned long long to_fixed(float v, float s1, float s2) {
+    return (unsigned long long)__float2ll_rn(__fmul_rn(__fmul_rn(v, s1), s2));
+}
+
+// ---------------------------------------------------------------------------
+// One slab (GP_SLAB sources starting at s0) of a tile.  SYM: also collect
+// the sums of the sources (off-diagonal tiles) into wpart[GP_SLAB][NC].
+// ---------------------------------------------------------------------------
+template <bool SYM, bool POT>
+__device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const float4 *__restrict__ dB,
+                                          int s0, int lane, const float2 (&nx)[GP_RP],
+                                          const float2 (&ny)[GP_RP], const float2 (&nz)[GP_RP],
+                                          const float2 (&mi)[GP_RP], float2 e2, float2 (&ax)[GP_RP],
+                                          float2 (&ay)[GP_RP], float2 (&az)[GP_RP],
+                                          float2 (&ap)[GP_RP], float *__restrict__ wpart, int tid) {
+    constexpr int NC = POT ? 4 : 3;
+    for (int c = 0; c < GP_SLAB / 32; ++c) {
+        float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;   // sums of the source this lane holds
+        const int cb = s0 + c * 32;
+#pragma unroll 1
+        for (int t = 0; t < 32; ++t) {
+            const int s = cb + ((lane + t) & 31);
+            const float4 a = dA[s];
+            const float4 b = dB[s];
+            const float2 qx = make_float2(a.x, a.y), qy = make_float2(a.z, a.w);
+            const float2 qz = make_float2(b.x, b.y), qm = make_float2(b.z, b.w);
+            float2 tx = make_float2(cx, 0.f), ty = make_float2(cy, 0.f), tz = make_float2(cz, 0.f);
+            float2 tp = make_float2(cp, 0.f);
+#pragma unroll
+            for (int p = 0; p < GP_RP; ++p) {
+                const float2 dx = __fadd2_rn(qx, nx[p]);
+                const float2 dy = __fadd2_rn(qy, ny[p]);
+                const float2 dz = __fadd2_rn(qz, nz[p]);
+                float2 r2 = __ffma2_rn(dx, dx, e2);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                if (!SYM && POT) {
+                    // diagonal tile: leave j = i out of the potential (targets
+                    // 2p and 2p + 1 of this thread are block entries
+                    // tid + 2p 256 and tid + (2p + 1) 256)
+                    if (s == tid + (2 * p) * GP_THREADS) inv.x = 0.f;
+                    if (s == tid + (2 * p + 1) * GP_THREADS) inv.y = 0.f;
+                }
+                const float2 w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+                const float2 si = __fmul2_rn(w, qm);
+                ax[p] = __ffma2_rn(si, dx, ax[p]);
+                ay[p] = __ffma2_rn(si, dy, ay[p]);
+                az[p] = __ffma2_rn(si, dz, az[p]);
+                if (POT) ap[p] = __ffma2_rn(qm, inv, ap[p]);
+                if (SYM) {
+                    const float2 sj = __fmul2_rn(w, mi[p]);
+                    tx = __ffma2_rn(sj, dx, tx);
+                    ty = __ffma2_rn(sj, dy, ty);
+                    tz = __ffma2_rn(sj, dz, tz);
+                    if (POT) tp = __ffma2_rn(mi[p], inv, tp);
+                }
+            }
+            if (SYM) {
+                const int from = (lane + 1) & 31;
+                cx = __shfl_sync(0xffffffffu, __fadd_rn(tx.x, tx.y), from);
+                cy = __shfl_sync(0xffffffffu, __fadd_rn(ty.x, ty.y), from);
+                cz = __shfl_sync(0xffffffffu, __fadd_rn(tz.x, tz.y), from);
+                if (POT) cp = __shfl_sync(0xffffffffu, __fadd_rn(tp.x, tp.y), from);
+            }
+        }
+        if (SYM) {
+            float *o = wpart + (c * 32 + lane) * NC;
+            o[0] = cx;
+            o[1] = cy;
+            o[2] = cz;
+            if (POT) o[3] = cp;
+        }
+    }
+}
+
+template <bool POT>
+__global__ void __launch_bounds__(GP_THREADS, 1)
+pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, float eps2,
+                        const PairsHeader *__restrict__ hdr,
+                        unsigned long long *__restrict__ acc) {
+    constexpr int NC = POT ? 4 : 3;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *dA = reinterpret_cast<float4 *>(smem);
+    float4 *dB = dA + GP_B;
+    float *part = reinterpret_cast<float *>(dB + GP_B);   // [warp][slab][NC]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int I, J;
+    tile_of(blockIdx.x, I, J);
+    const int cnt = min(GP_B, n - J * GP_B);
+    for (int q = tid; q < GP_B; q += GP_THREADS) {
+        const float4 v = q < cnt ? pos[(size_t)J * GP_B + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        dA[q] = make_float4(v.x, v.x, v.y, v.y);
+        dB[q] = make_float4(v.z, v.z, v.w, v.w);
+    }
+    // targets k of this thread: I B + tid + k 256; pair p = (2p, 2p + 1)
+    float2 nx[GP_RP], ny[GP_RP], nz[GP_RP], mi[GP_RP], ax[GP_RP], ay[GP_RP], az[GP_RP], ap[GP_RP];
+#pragma unroll
+    for (int p = 0; p < GP_RP; ++p) {
+        const int ia = I * GP_B + tid + (2 * p) * GP_THREADS, ib = ia + GP_THREADS;
+        const float4 a = ia < n ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = ib < n ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+        nx[p] = make_float2(-a.x, -b.x);
+        ny[p] = make_float2(-a.y, -b.y);
+        nz[p] = make_float2(-a.z, -b.z);
+        mi[p] = make_float2(a.w, b.w);
+        ax[p] = ay[p] = az[p] = ap[p] = make_float2(0.f, 0.f);
+    }
+    const float sa1 = hdr->s_acc1, sa2 = hdr->s_acc2, sp1 = hdr->s_pot1, sp2 = hdr->s_pot2;
+    __syncthreads();
+    const float2 e2 = make_float2(eps2, eps2);
+    float *wpart = part + warp * GP_SLAB * NC;
+    if (I != J) {
+        for (int s0 = 0; s0 < cnt; s0 += GP_SLAB) {   // sources past cnt are massless padding
+            ring_slab<true, POT>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+            __syncthreads();
+            for (int q = tid; q < GP_SLAB * NC; q += GP_THREADS) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < GP_WARPS; ++w) v = __fadd_rn(v, part[w * GP_SLAB * NC + q]);
+                const int j = J * GP_B + s0 + q / NC, comp = q % NC;
+                if (j < n)
+                    atomicAdd(&acc[(size_t)j * 4 + comp],
+                              comp < 3 ? to_fixed(-v, sa1, sa2) : to_fixed(v, sp1, sp2));
+            }
+            __syncthreads();   // warp sums consumed before the next slab
+        }
+    } else {
+        for (int s0 = 0; s0 < cnt; s0 += GP_SLAB)
+            ring_slab<false, POT>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+    }
+    // the tile's sums of its targets
+#pragma unroll
+    for (int p = 0; p < GP_RP; ++p) {
+        const int ia = I * GP_B + tid + (2 * p) * GP_THREADS, ib = ia + GP_THREADS;
+        if (ia < n) {
+            atomicAdd(&acc[(size_t)ia * 4 + 0], to_fixed(ax[p].x, sa1, sa2));
+            atomicAdd(&acc[(size_t)ia * 4 + 1], to_fixed(ay[p].x, sa1, sa2));
+            atomicAdd(&acc[(size_t)ia * 4 + 2], to_fixed(az[p].x, sa1, sa2));
+            if (POT) atomicAdd(&acc[(size_t)ia * 4 + 3], to_fixed(ap[p].x, sp1, sp2));
+        }
+        if (ib < n) {
+            atomicAdd(&acc[(size_t)ib * 4 + 0], to_fixed(ax[p].y, sa1, sa2));
+            atomicAdd(&acc[(size_t)ib * 4 + 1], to_fixed(ay[p].y, sa1, sa2));
+            atomicAdd(&acc[(size_t)ib * 4 + 2], to_fixed(az[p].y, sa1, sa2));
+            if (POT) atomicAdd(&acc[(size_t)ib * 4 + 3], to_fixed(ap[p].y, sp1, sp2));
+        }
+    }
+}
+
+// Fixed-point totals -> float4 (gx, gy, gz, phi).
+template <bool POT>
+__global__ void pairs_final_kernel(int n, float G, const PairsHeader *__restrict__ hdr,
+                                   const long long *__restrict__ acc, float4 *__restrict__ out,
+                                   int *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && hdr->status) atomicOr(flags, SPH_FLAG_GRAV_RANGE);
+    if (i >= n) return;
+    const double la = hdr->lsb_acc * (double)G;
+    const long long *a = acc + (size_t)i * 4;
+    const float phi = POT ? (float)(-(double)G * (double)a[3] * hdr->lsb_pot) : 0.f;
+    out[i] = make_float4((float)((double)a[0] * la), (float)((double)a[1] * la),
+                         (float)((double)a[2] * la), phi);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static std::once_flag g_pairs_once;
+static int g_pairs_status = SPH_OK;
+static int g_pairs_min_n = 65536;
+static std::mutex g_pairs_mutex;
+
+static void pairs_init() {
+    if (cudaFuncSetAttribute(pp_gravity_pairs_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(pp_gravity_pairs_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) != cudaSuccess)
+        g_pairs_status = SPH_ERR_CUDA;
+}
+
+}  // namespace sphgb
+
+using namespace sphgb;
+
+extern "C" size_t pp_gravity_pairs_workspace_bytes(int32_t n) {
+    if (n < 0) return 0;
+    return kPairsAccOffset + (size_t)n * 4 * sizeof(long long);
+}
+
+extern "C" int pp_gravity_pairs_min_n(int32_t n_min) {
+    if (n_min < 0) return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_pairs_mutex);
+    g_pairs_min_n = n_min ? n_min : 65536;
+    return SPH_OK;
+}
+
+extern "C" int pp_gravity_pairs_eligible(int32_t n, float eps, int32_t flags) {
+    int min_n;
+    {
+        std::lock_guard<std::mutex> lock(g_pairs_mutex);
+        min_n = g_pairs_min_n;
+    }
+    const float eps2 = eps * eps;
+    return (n >= min_n && n > 0 && eps2 > 0.0f && eps2 <= 3.0e38f &&
+            !(flags & SPH_GRAV_NO_KAHAN) && !gravity_plan_forced())
+               ? 1
+               : 0;
+}
+
+extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float eps,
+                                float *d_acc_pot, int32_t flags, void *d_work, size_t work_bytes,
+                                sph_stream_t stream) {
+    if (n < 0 || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
+    if (n == 0) return SPH_OK;
+    if (!pp_gravity_pairs_eligible(n, eps, flags) || !d_work ||
+        work_bytes < pp_gravity_pairs_workspace_bytes(n))
+        return pp_gravity(d_pos_m, n, G, eps, d_acc_pot, flags, stream);
+    if (!d_pos_m || !d_acc_pot) return SPH_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_pos_m) & 15u) ||
+        (reinterpret_cast<uintptr_t>(d_acc_pot) & 15u) ||
+        (reinterpret_cast<uintptr_t>(d_work) & 255u))
+        return SPH_ERR_INVALID_ARG;
+    std::call_once(g_pairs_once, pairs_init);
+    if (g_pairs_status != SPH_OK) return g_pairs_status;
+    int *flags_dev = gravity_flags_device();
+    if (!flags_dev) return SPH_ERR_CUDA;
+    const long long nb = (n + GP_B - 1) / GP_B;
+    const long long n_tiles = nb * (nb + 1) / 2;
+    if (n_tiles > 0x7fffffffll) return SPH_ERR_INVALID_ARG;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool pot = flags & SPH_GRAV_POTENTIAL;
+    const float4 *pos = reinterpret_cast<const float4 *>(d_pos_m);
+    PairsHeader *hdr = static_cast<PairsHeader *>(d_work);
+    unsigned long long *acc =
+        reinterpret_cast<unsigned long long *>(static_cast<unsigned char *>(d_work) + kPairsAccOffset);
+    const float eps2 = eps * eps;
+    SPH_CUDA_TRY(cudaMemsetAsync(d_work, 0, pp_gravity_pairs_workspace_bytes(n), st));
+    pairs_mass_kernel<<<GP_MASS_BLOCKS, 256, 0, st>>>(pos, n, hdr);
+    pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr);
+    if (pot)
+        pp_gravity_pairs_kernel<true><<<(unsigned)n_tiles, GP_THREADS, GP_SMEM, st>>>(pos, n, eps2, hdr, acc);
+    else
+        pp_gravity_pairs_kernel<false><<<(unsigned)n_tiles, GP_THREADS, GP_SMEM, st>>>(pos, n, eps2, hdr, acc);
+    const long long *acc_s = reinterpret_cast<const long long *>(acc);
+    float4 *out = reinterpret_cast<float4 *>(d_acc_pot);
+    if (pot)
+        pairs_final_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
+    else
+        pairs_final_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
+    note_launch(4);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}

@@ -28,6 +28,10 @@ int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *unit
                            int *counter, int R, float G, float eps, float4 *out, int flags,
                            cudaStream_t st);
 int gravity_num_sms();
+// device address of the gravity kernels' status word (SPH_FLAG_*)
+int *gravity_flags_device();
+// true while sph_gravity_tune has fixed a one-sided launch plan
+bool gravity_plan_forced();
 
 // neighbors.cu
 struct NbArgs {

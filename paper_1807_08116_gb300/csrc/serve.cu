@@ -98,8 +98,13 @@ struct Job {
     bool rhs_done = false;
 };
 
-size_t state_bytes(int n, int ng) {
-    size_t b = 0;
+// Scratch of the pair-once gravity kernel for jobs it applies to (0 if none).
+size_t pairs_bytes(const SphParams &p, int n) {
+    return pp_gravity_pairs_eligible(n, p.eps, 0) ? pp_gravity_pairs_workspace_bytes(n) : 0;
+}
+
+size_t state_bytes(int n, int ng, size_t grav_work) {
+    size_t b = up256(grav_work);
     b += up256(3 * sizeof(double) * n) * 3;            // r, v, v_save
     b += up256(sizeof(double) * ng) * 2;               // e, e_save
     b += up256(sizeof(float) * n) + up256(sizeof(float) * ng);   // mass, h
@@ -109,7 +114,7 @@ size_t state_bytes(int n, int ng) {
     return b;
 }
 
-void carve_state(Job &j, char *base) {
+void carve_state(Job &j, char *base, size_t grav_work) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
         char *p = base + o;
@@ -135,6 +140,8 @@ void carve_state(Job &j, char *base) {
     j.st.fresh = 0;
     j.st.grav_flags = 0;
     j.st.events = nullptr;
+    j.st.grav_work = grav_work ? take(grav_work) : nullptr;
+    j.st.grav_work_bytes = grav_work;
 }
 
 int log2_buckets(int ng) {
@@ -219,10 +226,11 @@ int size_lists(sph_server *s, Job &j, cudaStream_t st) {
 
 // Admit job j: state + context out of the arena, upload the IC, size lists.
 int admit(sph_server *s, Job &j, cudaStream_t st) {
-    j.state_bytes = state_bytes(j.n, j.n_gas);
+    const size_t gw = pairs_bytes(s->params, j.n);
+    j.state_bytes = state_bytes(j.n, j.n_gas, gw);
     if (!s->arena.alloc(j.state_bytes, &j.state_off)) return SPH_ERR_BUDGET;
     j.has_state = true;
-    carve_state(j, s->arena_base + j.state_off);
+    carve_state(j, s->arena_base + j.state_off, gw);
     j.log2_M = log2_buckets(j.n_gas);
     int rc = make_ctx(s, j, std::max<long long>(1024, (long long)j.n_gas * 120), st);
     if (rc) {
@@ -310,7 +318,7 @@ extern "C" int sim_submit(sph_server *s, const SimRequest *req, uint64_t *job_id
         (req->n_gas > 0 && (!req->h_e || !req->h_h)))
         return SPH_ERR_INVALID_ARG;
     // a request that can never fit the budget is refused at once
-    const size_t est = state_bytes(req->n, req->n_gas) +
+    const size_t est = state_bytes(req->n, req->n_gas, pairs_bytes(s->params, req->n)) +
                        sph_ctx_workspace_bytes(std::max(1, req->n_gas), log2_buckets(req->n_gas),
                                                std::max<long long>(1024, (long long)req->n_gas * 120));
     std::lock_guard<std::mutex> lock(s->mu);

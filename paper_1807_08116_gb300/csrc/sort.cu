@@ -117,9 +117,11 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restri
     __syncthreads();
     const GridDev g = *gridp;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int l = -1;                 // level of this thread's particle (-1: none)
+    unsigned hb = 0u;
     if (i < n) {
         float4 p = pos_h[i];
-        int l = level_of(p.w, g.log2_L0, g.n_levels);
+        l = level_of(p.w, g.log2_L0, g.n_levels);
         float inv_c = pow2f(-g.log2_L0 - l);
         int cx = cell_of(p.x, g.x0, inv_c);
         int cy = cell_of(p.y, g.y0, inv_c);
@@ -129,16 +131,27 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restri
         const int sim = sim_of ? sim_of[i] : 0;
         int k = bucket_of(cx, cy, cz, l + kMaxLevels * sim, g.log2_M);
         key[i] = k;
+        hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
+        // The occupancy word and the bucket's h maximum are shared by every
+        // particle of a dense super-cell / bucket: read before the atomic so
+        // that only the particles that change them contend (both only grow
+        // within a launch, so a stale read costs one redundant atomic).
         if (occ) {
             const unsigned b = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
                                          l + kMaxLevels * sim, log2_B);
-            atomicOr(&occ[b >> 5], 1u << (b & 31));
+            const unsigned bit = 1u << (b & 31);
+            if (!(__ldcg(&occ[b >> 5]) & bit)) atomicOr(&occ[b >> 5], bit);
         }
         atomicAdd(&count[k], 1);
-        unsigned hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
-        atomicMax(&hmax_cell[k], hb);
-        atomicAdd(&s_cnt[l], 1);
-        atomicMax(&s_hmax[l], hb);
+        if (__ldcg(&hmax_cell[k]) < hb) atomicMax(&hmax_cell[k], hb);
+    }
+    // per-level totals: one shared atomic per (warp, level) instead of one
+    // per particle
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    const unsigned hpeer = __reduce_max_sync(peers, hb);
+    if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+        atomicAdd(&s_cnt[l], __popc(peers));
+        atomicMax(&s_hmax[l], hpeer);
     }
     __syncthreads();
     if (threadIdx.x < kMaxLevels && s_cnt[threadIdx.x]) {

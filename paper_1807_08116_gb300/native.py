@@ -30,6 +30,7 @@ SPH_FLAG_NB_OVERFLOW = 1
 SPH_FLAG_SEARCH_WIDE = 2
 SPH_FLAG_TIMEOUT = 4
 SPH_FLAG_ROW_UNSORTED = 8
+SPH_FLAG_GRAV_RANGE = 16
 
 SPH_GRAV_POTENTIAL = 1
 SPH_GRAV_NO_KAHAN = 2
@@ -60,7 +61,8 @@ class SphState(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_gas", ctypes.c_int32)] + [
         (k, ctypes.c_void_p) for k in ("r", "v", "e", "v_save", "e_save", "mass", "h", "pos_m",
                                        "pos_h", "vel_e", "rho", "acc_hyd", "grav")] + [
-        ("fresh", ctypes.c_int32), ("grav_flags", ctypes.c_int32), ("events", ctypes.c_void_p)]
+        ("fresh", ctypes.c_int32), ("grav_flags", ctypes.c_int32), ("events", ctypes.c_void_p),
+        ("grav_work", ctypes.c_void_p), ("grav_work_bytes", ctypes.c_size_t)]
 
 class SimRequest(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_gas", ctypes.c_int32), ("n_steps", ctypes.c_int32),
@@ -124,6 +126,11 @@ def lib():
             "sph_cfl_dt": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
             "pp_gravity": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "pp_gravity_status": (_I, [_P, ctypes.POINTER(_I)]),
+            "pp_gravity_pairs": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P,
+                                      ctypes.c_size_t, _P]),
+            "pp_gravity_pairs_workspace_bytes": (ctypes.c_size_t, [_I]),
+            "pp_gravity_pairs_eligible": (_I, [_I, ctypes.c_float, _I]),
+            "pp_gravity_pairs_min_n": (_I, [_I]),
             "sph_gravity_plan": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
             "sph_gravity_tune": (_I, [_I, _I]),
             "integrate_step": (_I, [_I, ctypes.c_double, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -340,6 +347,38 @@ def pp_gravity(pos_m, acc_pot, G=1.0, eps=0.01, flags=0, stream=None):
     _check("pp_gravity", rc)
 
 
+def pp_gravity_pairs_workspace_bytes(n):
+    return int(lib().pp_gravity_pairs_workspace_bytes(int(n)))
+
+
+def pp_gravity_pairs_workspace(n, device="cuda"):
+    """A scratch tensor for pp_gravity_pairs over n bodies (256-byte aligned)."""
+    nbytes = pp_gravity_pairs_workspace_bytes(n)
+    return torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=device)
+
+
+def pp_gravity_pairs(pos_m, acc_pot, work, G=1.0, eps=0.01, flags=0, stream=None):
+    """Gravity with every pair evaluated once (falls back to pp_gravity when not
+    eligible or `work` is None / too small)."""
+    n = pos_m.shape[0]
+    wp, wb = (None, 0) if work is None else (work.data_ptr(), work.numel() * work.element_size())
+    if work is not None and (not work.is_cuda or not work.is_contiguous()):
+        raise ValueError("work: contiguous CUDA tensor expected")
+    rc = lib().pp_gravity_pairs(_ptr(pos_m, torch.float32, (n, 4), "pos_m"), n, float(G),
+                                float(eps), _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"),
+                                int(flags), wp, wb, _stream(stream))
+    _check("pp_gravity_pairs", rc)
+
+
+def pp_gravity_pairs_eligible(n, eps=0.01, flags=0):
+    return bool(lib().pp_gravity_pairs_eligible(int(n), float(eps), int(flags)))
+
+
+def pp_gravity_pairs_min_n(n_min=0):
+    """Smallest n for the pair-once kernel (0: default)."""
+    _check("pp_gravity_pairs_min_n", lib().pp_gravity_pairs_min_n(int(n_min)))
+
+
 def pp_gravity_status(stream=None):
     f = _I()
     rc = lib().pp_gravity_status(_stream(stream), ctypes.byref(f))
@@ -383,9 +422,11 @@ def state_struct(t: dict, n, n_gas, fresh=0, grav_flags=0):
     def p(k):
         x = t.get(k)
         return None if x is None else x.data_ptr()
+    gw = t.get("grav_work")
     return SphState(n, n_gas, p("r"), p("v"), p("e"), p("v_save"), p("e_save"), p("mass"),
                     p("h"), p("pos_m"), p("pos_h"), p("vel_e"), p("rho"), p("acc_hyd"),
-                    p("grav"), int(fresh), int(grav_flags), None)
+                    p("grav"), int(fresh), int(grav_flags), None, p("grav_work"),
+                    0 if gw is None else gw.numel() * gw.element_size())
 
 
 class StageEvents:

@@ -41,7 +41,7 @@ class Simulation:
     memory and advanced by sph_step."""
 
     def __init__(self, ic: dict, device=None, grav_flags=0, nb_per_particle=120,
-                 batch_offsets=None, **params):
+                 batch_offsets=None, pairs=True, **params):
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
         self.params = dict(nv.DEFAULT_PARAMS)
@@ -65,8 +65,13 @@ class Simulation:
         t["rho"] = torch.zeros(ng, **f32)
         t["acc_hyd"] = torch.zeros((ng, 4), **f32)
         t["grav"] = torch.zeros((n, 4), **f32)
-        self.t = t
         self.grav_flags = int(grav_flags)
+        # scratch of the pair-once gravity kernel (single simulations; a batch
+        # uses the batched one-sided kernel)
+        if (pairs and batch_offsets is None and
+                nv.pp_gravity_pairs_eligible(n, self.params["eps"], self.grav_flags)):
+            t["grav_work"] = nv.pp_gravity_pairs_workspace(n, device=dev)
+        self.t = t
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)
         self.ctx = None
         self.lanes = None

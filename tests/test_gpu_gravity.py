@@ -39,13 +39,18 @@ def test_single_halo_all_rows(orc):
 def test_ragged_sizes(orc, n):
     rng = np.random.default_rng(n)
     pm = pos_m_of(rng.normal(size=(n, 3)), rng.uniform(0.5, 1.5, n) / n)
-    g = _gpu_gravity(pm, G=0.7, eps=0.05)
-    acc, _ = orc.gravity(pm, G=0.7, eps=0.05)
+    from paper_1807_08116_gb300 import native as nv
+    g = _gpu_gravity(pm, G=0.7, eps=0.05, flags=nv.SPH_GRAV_POTENTIAL)
+    acc, pot = orc.gravity(pm, G=0.7, eps=0.05)
     if n == 1:
-        assert np.all(g[:, :3] == 0.0)
+        assert np.all(g == 0.0)      # no other body: no force, no potential
         return
     rms, mx = err(g[:, :3], acc)
     assert rms <= RMS_TOL and mx <= MAX_TOL, (rms, mx)
+    # the potential leaves j = i out inside the sum (not subtracted after it),
+    # so it stays accurate when the self term m_i / eps would dominate
+    prms, pmx = err(g[:, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL, (prms, pmx)
 
 
 def test_empty_is_noop():

@@ -1,0 +1,190 @@
+"""pp_gravity_pairs (Eq. 4 with every pair evaluated once) through the C ABI
+against the FP64 oracle: ragged block counts, the diagonal-only case, the
+potential and its self term, bitwise reproducibility, the fall-backs to the
+one-sided kernel, and whole simulations that take the pair-once path."""
+import numpy as np
+import pytest
+
+from helpers import MAX_TOL, RMS_TOL, err, need_gpu, pos_m_of
+from paper_1807_08116_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def low_threshold():
+    """Use the pair-once kernel down to n = 1 for the duration of a test."""
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    nv.pp_gravity_pairs_min_n(1)
+    try:
+        yield nv
+    finally:
+        nv.pp_gravity_pairs_min_n(0)
+
+
+def _pairs(pm, G=1.0, eps=0.01, flags=0, work=True):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    x = torch.as_tensor(pm, device="cuda")
+    out = torch.full_like(x, float("nan"))
+    w = nv.pp_gravity_pairs_workspace(len(pm)) if work else None
+    nv.pp_gravity_pairs(x, out, w, G=G, eps=eps, flags=flags)
+    torch.cuda.synchronize()
+    assert nv.pp_gravity_status() == 0
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _onesided(pm, G=1.0, eps=0.01, flags=0):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    x = torch.as_tensor(pm, device="cuda")
+    out = torch.full_like(x, float("nan"))
+    nv.pp_gravity(x, out, G=G, eps=eps, flags=flags)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_workspace_size_and_eligibility():
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    assert nv.pp_gravity_pairs_workspace_bytes(0) == 4096
+    assert nv.pp_gravity_pairs_workspace_bytes(1000) == 4096 + 32 * 1000
+    assert nv.pp_gravity_pairs_eligible(65536, 0.01)
+    assert not nv.pp_gravity_pairs_eligible(65535, 0.01)
+    assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.0)            # unsoftened
+    assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.01, nv.SPH_GRAV_NO_KAHAN)
+    nv.sph_gravity_tune(4, 1)
+    try:
+        assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.01)       # a fixed one-sided plan
+    finally:
+        nv.sph_gravity_tune(0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 2047, 2048, 2049, 4096, 5000, 9999])
+def test_ragged_block_counts(orc, low_threshold, n):
+    # 1 block (diagonal tile only) up to 5 blocks with a ragged last block
+    nv = low_threshold
+    rng = np.random.default_rng(n)
+    pm = pos_m_of(rng.normal(size=(n, 3)), rng.uniform(0.5, 1.5, n) / n)
+    g = _pairs(pm, G=0.7, eps=0.05, flags=nv.SPH_GRAV_POTENTIAL)
+    acc, pot = orc.gravity(pm, G=0.7, eps=0.05)
+    if n == 1:
+        assert np.all(g == 0.0)      # the self term of the potential cancels exactly
+        return
+    rms, mx = err(g[:, :3], acc)
+    assert rms <= RMS_TOL and mx <= MAX_TOL, (rms, mx)
+    prms, pmx = err(g[:, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL, (prms, pmx)
+
+
+def test_single_halo_all_rows_and_momentum(orc, low_threshold):
+    nv = low_threshold
+    d = ics.single_halo(8192, 8192, seed=0)
+    pm = pos_m_of(d["r"], d["m"])
+    g = _pairs(pm, flags=nv.SPH_GRAV_POTENTIAL)
+    acc, pot = orc.gravity(pm)
+    rms, mx = err(g[:, :3], acc)
+    print(f"pairs 16384: rms {rms:.2e} max {mx:.2e}")
+    assert rms <= RMS_TOL and mx <= MAX_TOL
+    prms, pmx = err(g[:, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL
+    # each pair's two contributions are exact negatives before the fixed-point
+    # rounding of the tile sums: total momentum change at that rounding level
+    m = pm[:, 3].astype(np.float64)
+    assert np.abs((m[:, None] * g[:, :3]).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(g[:, :3])).sum()
+
+
+def test_bitwise_reproducible(low_threshold):
+    rng = np.random.default_rng(3)
+    n = 70001
+    pm = pos_m_of(rng.normal(size=(n, 3)), rng.uniform(0.5, 1.5, n) / n)
+    a = _pairs(pm, flags=low_threshold.SPH_GRAV_POTENTIAL)
+    b = _pairs(pm, flags=low_threshold.SPH_GRAV_POTENTIAL)
+    assert np.array_equal(a, b)
+
+
+def test_fallbacks_equal_onesided(low_threshold):
+    nv = low_threshold
+    rng = np.random.default_rng(5)
+    pm = pos_m_of(rng.uniform(-1, 1, size=(3000, 3)), np.full(3000, 1e-3))
+    # unsoftened: the one-sided kernel with its coincident-pair guard
+    assert np.array_equal(_pairs(pm, eps=0.0), _onesided(pm, eps=0.0))
+    # NO_KAHAN asks for the one-sided plain sums
+    f = nv.SPH_GRAV_NO_KAHAN
+    assert np.array_equal(_pairs(pm, flags=f), _onesided(pm, flags=f))
+    # no scratch
+    assert np.array_equal(_pairs(pm, work=False), _onesided(pm))
+    # a fixed one-sided plan
+    nv.sph_gravity_tune(2, 1)
+    try:
+        assert np.array_equal(_pairs(pm), _onesided(pm))
+    finally:
+        nv.sph_gravity_tune(0)
+
+
+def test_scale_follows_units(orc, low_threshold):
+    # the fixed-point scale comes from sum |m| and eps: tiny and huge unit
+    # systems give the same relative accuracy
+    rng = np.random.default_rng(8)
+    n = 3000
+    r = rng.normal(size=(n, 3))
+    m = rng.uniform(0.5, 1.5, n) / n
+    for L, M in ((1e-6, 1e-20), (1e5, 1e25)):
+        pm = pos_m_of(r * L, m * M)
+        g = _pairs(pm, G=1.0, eps=0.05 * L)
+        acc, _ = orc.gravity(pm, G=1.0, eps=0.05 * L)
+        rms, mx = err(g[:, :3], acc)
+        assert rms <= RMS_TOL and mx <= MAX_TOL, (L, M, rms, mx)
+
+
+def test_two_halo_sampled_rows(orc):
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    d = ics.two_halo(131072, 131072, seed=1)
+    pm = pos_m_of(d["r"], d["m"])
+    assert nv.pp_gravity_pairs_eligible(len(pm), 0.01)
+    g = _pairs(pm, flags=nv.SPH_GRAV_POTENTIAL)
+    rows = np.random.default_rng(0).choice(len(pm), 512, replace=False)
+    acc, pot = orc.gravity(pm, rows=rows)
+    rms, mx = err(g[rows, :3], acc)
+    print(f"pairs 524288 sample: rms {rms:.2e} max {mx:.2e}")
+    assert rms <= RMS_TOL and mx <= MAX_TOL
+    prms, pmx = err(g[rows, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL
+
+
+def test_large_collision_sampled_rows(orc):
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    d = ics.two_halo(1048576, 1048576, seed=2)
+    pm = pos_m_of(d["r"], d["m"])
+    g = _pairs(pm)
+    rows = np.random.default_rng(1).choice(len(pm), 256, replace=False)
+    acc, _ = orc.gravity(pm, rows=rows)
+    rms, mx = err(g[rows, :3], acc)
+    print(f"pairs 4194304 sample: rms {rms:.2e} max {mx:.2e}")
+    assert rms <= RMS_TOL and mx <= MAX_TOL
+
+
+def test_simulation_takes_pair_path(orc):
+    need_gpu()
+    from paper_1807_08116_gb300.sim import Simulation
+    d = ics.two_halo(32768, 32768, seed=12)
+    sim = Simulation(d)
+    assert "grav_work" in sim.t
+    sim.initial_rhs()
+    rows = np.random.default_rng(2).choice(d["n"], 256, replace=False)
+    pm = pos_m_of(d["r"], d["m"])
+    acc, _ = orc.gravity(pm, rows=rows)
+    g = sim.t["grav"].cpu().numpy().astype(np.float64)
+    rms, mx = err(g[rows, :3], acc)
+    assert rms <= RMS_TOL and mx <= MAX_TOL
+    sim.step(1e-3)
+    # the same run with the one-sided kernel agrees to force rounding
+    ref = Simulation(d, pairs=False)
+    assert "grav_work" not in ref.t
+    ref.initial_rhs()
+    ref.step(1e-3)
+    rv, _ = err(sim.velocities(), ref.velocities())
+    assert rv < 1e-6
