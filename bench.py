@@ -432,8 +432,11 @@ def run_ensemble(args):
     # (a) batched
     bsim = Simulation(ic, batch_offsets=(go, do, so))
     bsim.initial_rhs()
-    from paper_1807_08116_gb300.tune import tune_batch
-    best_R, tune = tune_batch(bsim.batch, bsim.t["pos_m"], reps=3)
+    pairs = "grav_work" in bsim.t   # pair-once gravity over all simulations' tiles
+    best_R, tune = None, None
+    if not pairs:
+        from paper_1807_08116_gb300.tune import tune_batch
+        best_R, tune = tune_batch(bsim.batch, bsim.t["pos_m"], reps=3)
     for _ in range(args.warmup):
         bsim.step(dt)
     bsim.capture(dt)
@@ -473,6 +476,8 @@ def run_ensemble(args):
         "config": {"workload": f"ensemble of {args.n_sims} two-halo collisions, "
                                "N log-uniform in [8192, 262144], b ~ U[0,4a], v ~ U[0.5,2] v_esc",
                    "n_total": n_tot, "n_sims": args.n_sims, "cuda_graph": True,
+                   "gravity": ("pair-once, one launch over the tiles of every simulation" if pairs
+                               else "one-sided persistent work queue"),
                    "gravity_units_R": best_R, "autotune_ms": tune},
         "max_rel_position_diff_batched_vs_sequential": worst,
         "interactions_per_step": float(sum(d["n"] ** 2 for d in lst)),

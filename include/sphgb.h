@@ -400,8 +400,19 @@ int sph_batch_set_plan(sph_batch *b, int32_t R, sph_stream_t stream);
 int pp_gravity_batched(const sph_batch *b, const float *d_pos_m, float G, float eps,
                        float *d_acc_pot, int32_t flags, sph_stream_t stream);
 
+/* pp_gravity_pairs for every simulation of the batch in one launch: the
+ * tiles of all simulations' triangles, one CTA each, fixed-point sums over
+ * the batch's n particles (scale from the whole batch's sum |m|).  d_work as
+ * for pp_gravity_pairs(b's n); runs pp_gravity_batched when not eligible
+ * (pp_gravity_pairs_eligible on the batch's n) or d_work is missing / too
+ * small. */
+int pp_gravity_pairs_batched(const sph_batch *b, const float *d_pos_m, float G, float eps,
+                             float *d_acc_pot, int32_t flags, void *d_work, size_t work_bytes,
+                             sph_stream_t stream);
+
 /* Attach a batch to a context (NULL detaches): later sorts use the batch's
- * simulation map, and sph_rhs_initial / sph_step use pp_gravity_batched. */
+ * simulation map, and sph_rhs_initial / sph_step use pp_gravity_pairs_batched
+ * (state with grav_work) or pp_gravity_batched. */
 int sph_ctx_set_batch(sph_ctx *ctx, const sph_batch *b);
 
 /* ------------------------------------------------------------------------ */

@@ -90,6 +90,8 @@ struct sph_batch {
     int *d_counter;
     size_t units_cap;
     const int *d_sim_of_gas;
+    long long *d_tile_off;       // pair-once gravity: first tile of each simulation [n_sims + 1]
+    long long n_pair_tiles;
 };
 
 namespace {
@@ -457,6 +459,9 @@ int gravity_of(sph_ctx *ctx, SphState *s, sph_stream_t stream) {
     const float G = ctx ? ctx->params.G : 1.0f, eps = ctx ? ctx->params.eps : 0.0f;
     if (ctx && ctx->batch) {
         if (ctx->batch->n != s->n || ctx->batch->n_gas != s->n_gas) return SPH_ERR_INVALID_ARG;
+        if (s->grav_work)
+            return pp_gravity_pairs_batched(ctx->batch, s->pos_m, G, eps, s->grav, s->grav_flags,
+                                            s->grav_work, s->grav_work_bytes, stream);
         return pp_gravity_batched(ctx->batch, s->pos_m, G, eps, s->grav, s->grav_flags, stream);
     }
     if (s->grav_work)
@@ -578,7 +583,7 @@ size_t batch_units_cap(int n_sims, const int32_t *g, const int32_t *d) {
 }
 
 struct BatchCarve {
-    size_t sims, units, counter, total;
+    size_t sims, units, counter, tile_off, total;
 };
 
 BatchCarve batch_carve(int n_sims, size_t units_cap) {
@@ -587,7 +592,8 @@ BatchCarve batch_carve(int n_sims, size_t units_cap) {
     c.sims = 0;
     c.units = up(sizeof(int4) * (size_t)n_sims);
     c.counter = c.units + up(sizeof(int2) * units_cap);
-    c.total = c.counter + 256;
+    c.tile_off = c.counter + 256;
+    c.total = c.tile_off + up(sizeof(long long) * ((size_t)n_sims + 1));
     return c;
 }
 
@@ -647,10 +653,17 @@ extern "C" int sph_batch_create(int32_t n_sims, const int32_t *h_gas_off, const 
     b->d_counter = reinterpret_cast<int *>(base + c.counter);
     b->units_cap = cap;
     b->d_sim_of_gas = d_sim_of_gas;
+    b->d_tile_off = reinterpret_cast<long long *>(base + c.tile_off);
+    std::vector<long long> tile_off(n_sims + 1, 0);
+    for (int s = 0; s < n_sims; ++s)
+        tile_off[s + 1] = tile_off[s] + pairs_tiles((long long)b->h_sims[s].y + b->h_sims[s].w);
+    b->n_pair_tiles = tile_off[n_sims];
     cudaStream_t st = (cudaStream_t)stream;
     int rc = SPH_OK;
     if (cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(int4) * n_sims, cudaMemcpyHostToDevice,
-                        st) != cudaSuccess)
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_tile_off, tile_off.data(), sizeof(long long) * (n_sims + 1),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = SPH_ERR_CUDA;
     if (rc == SPH_OK) rc = batch_build_units(b, 4, st);
     if (rc == SPH_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPH_ERR_CUDA;
@@ -684,6 +697,23 @@ extern "C" int pp_gravity_batched(const sph_batch *b, const float *d_pos_m, floa
     return launch_gravity_batched(reinterpret_cast<const float4 *>(d_pos_m), b->d_sims, b->d_units,
                                   (int)b->h_units.size(), b->d_counter, b->R, G, eps,
                                   reinterpret_cast<float4 *>(d_acc_pot), flags, (cudaStream_t)stream);
+}
+
+extern "C" int pp_gravity_pairs_batched(const sph_batch *b, const float *d_pos_m, float G,
+                                        float eps, float *d_acc_pot, int32_t flags, void *d_work,
+                                        size_t work_bytes, sph_stream_t stream) {
+    if (!b || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
+    if (b->n == 0) return SPH_OK;
+    if (!pp_gravity_pairs_eligible(b->n, eps, flags) || !d_work ||
+        work_bytes < pp_gravity_pairs_workspace_bytes(b->n))
+        return pp_gravity_batched(b, d_pos_m, G, eps, d_acc_pot, flags, stream);
+    if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot) ||
+        (reinterpret_cast<uintptr_t>(d_work) & 255u))
+        return SPH_ERR_INVALID_ARG;
+    return launch_gravity_pairs_batched(reinterpret_cast<const float4 *>(d_pos_m), b->n, b->d_sims,
+                                        b->d_tile_off, b->n_sims, b->n_pair_tiles, G, eps,
+                                        reinterpret_cast<float4 *>(d_acc_pot), flags, d_work,
+                                        (cudaStream_t)stream);
 }
 
 extern "C" int sph_ctx_set_batch(sph_ctx *ctx, const sph_batch *b) {

@@ -10,7 +10,8 @@
 //
 // Layout of the work:
 //  * bodies are cut into blocks of B = 2048 (256 threads x 8 targets); the
-//    block pairs (I <= J) of the triangle are the tiles, one CTA each.  A
+//    block pairs (I <= J) of the triangle are the tiles, one CTA each,
+//    visited in 16 x 16 super-tiles for L2 locality.  A
 //    diagonal tile (I, I) is evaluated one-sided (every target against every
 //    source of the block, j = i left out of the potential); an off-diagonal
 //    tile evaluates each of its B x B pairs once.
@@ -58,7 +59,8 @@ constexpr int GP_SLAB = 256;                  // sources per cross-warp reductio
 constexpr int GP_MASS_BLOCKS = 256;
 constexpr int GP_SMEM_DUP = 2 * GP_B * 16;                  // (x, x, y, y), (z, z, m, m)
 constexpr int GP_SMEM_PART = GP_WARPS * GP_SLAB * 4 * 4;    // warp sums of a slab
-constexpr int GP_SMEM = GP_SMEM_DUP + GP_SMEM_PART;
+constexpr int GP_SMEM_IDX = 2 * GP_B * 4;                  // global indices of the tile
+constexpr int GP_SMEM = GP_SMEM_DUP + GP_SMEM_PART + GP_SMEM_IDX;
 static_assert(GP_SMEM <= 227 * 1024, "shared memory of the pair kernel");
 static_assert(GP_B % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
 
@@ -74,14 +76,30 @@ struct PairsHeader {
 constexpr size_t kPairsAccOffset = 4096;
 static_assert(sizeof(PairsHeader) <= kPairsAccOffset, "pairs header");
 
-// Tile b of the triangle -> (I, J), I <= J: tiles are numbered by J, then I
-// (b = J (J + 1) / 2 + I), so CTAs that run together share a source block.
-__device__ __forceinline__ void tile_of(long long b, int &I, int &J) {
+// Entry b of a triangle -> (I, J), I <= J, numbered by J, then I
+// (b = J (J + 1) / 2 + I).
+__device__ __forceinline__ void tri_of(long long b, int &I, int &J) {
     int j = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
     while ((long long)j * (j + 1) / 2 > b) --j;
     while ((long long)(j + 1) * (j + 2) / 2 <= b) ++j;
     J = j;
     I = (int)(b - (long long)j * (j + 1) / 2);
+}
+
+// CTA b -> tile (I, J).  Tiles are visited in super-tiles of 16 x 16 (the
+// super-tiles themselves in triangle order, the tiles inside row by row), so
+// the CTAs resident at one time touch about 16 target blocks and 16 source
+// blocks: their sources and the fixed-point sums they add to stay in L2.
+// Returns false for the cells of a super-tile below the diagonal or past the
+// last block (those CTAs exit at once).
+constexpr int GP_SUPER = 16;
+__device__ __forceinline__ bool tile_of(long long b, int nb, int &I, int &J) {
+    int P, Q;
+    tri_of(b / (GP_SUPER * GP_SUPER), P, Q);
+    const int local = (int)(b % (GP_SUPER * GP_SUPER));
+    I = P * GP_SUPER + local / GP_SUPER;
+    J = Q * GP_SUPER + local % GP_SUPER;
+    return I <= J && J < nb;
 }
 
 // ---------------------------------------------------------------------------
@@ -219,32 +237,70 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
     }
 }
 
-template <bool POT>
+// One tile per CTA.  BATCH: many independent simulations; simulation s owns
+// the tiles [tile_off[s], tile_off[s + 1]) of its own triangle, over its
+// virtual bodies 0..ns-1 (virtual v < ng is global g0 + v, else d0 + v - ng).
+// In a batch, the global index of every target and source of the tile (-1
+// for padding) is kept in shared memory for the atomics; one simulation
+// computes them (the shared-memory form cost 1.5% there).
+template <bool POT, bool BATCH>
 __global__ void __launch_bounds__(GP_THREADS, 1)
-pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, float eps2,
-                        const PairsHeader *__restrict__ hdr,
+pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb,
+                        const int4 *__restrict__ sims, const long long *__restrict__ tile_off,
+                        int n_sims, float eps2, const PairsHeader *__restrict__ hdr,
                         unsigned long long *__restrict__ acc) {
     constexpr int NC = POT ? 4 : 3;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *dA = reinterpret_cast<float4 *>(smem);
     float4 *dB = dA + GP_B;
-    float *part = reinterpret_cast<float *>(dB + GP_B);   // [warp][slab][NC]
+    float *part = reinterpret_cast<float *>(dB + GP_B);                   // [warp][slab][NC]
+    int *sidx = reinterpret_cast<int *>(smem + GP_SMEM_DUP + GP_SMEM_PART);  // [GP_B] sources
+    int *tidx = sidx + GP_B;                                               // [GP_B] targets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int I, J;
-    tile_of(blockIdx.x, I, J);
-    const int cnt = min(GP_B, n - J * GP_B);
+    int I, J, g0 = 0, ng = n, d0 = 0, ns = n;
+    if (BATCH) {
+        const long long b = blockIdx.x;
+        int lo = 0, hi = n_sims - 1;   // last simulation whose first tile is <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_off[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        const int4 sd = sims[lo];
+        g0 = sd.x;
+        ng = sd.y;
+        d0 = sd.z;
+        ns = sd.y + sd.w;
+        tri_of(b - tile_off[lo], I, J);
+    } else if (!tile_of(blockIdx.x, nb, I, J)) {
+        return;
+    }
+    auto global_of = [&](int v) { return v < ng ? g0 + v : d0 + (v - ng); };
+    const int cnt = min(GP_B, ns - J * GP_B);
     for (int q = tid; q < GP_B; q += GP_THREADS) {
-        const float4 v = q < cnt ? pos[(size_t)J * GP_B + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int gi = -1;
+        if (q < cnt) {
+            gi = global_of(J * GP_B + q);
+            v = pos[gi];
+        }
+        if (BATCH) sidx[q] = gi;
         dA[q] = make_float4(v.x, v.x, v.y, v.y);
         dB[q] = make_float4(v.z, v.z, v.w, v.w);
     }
-    // targets k of this thread: I B + tid + k 256; pair p = (2p, 2p + 1)
+    // targets k of this thread: block entries tid + k 256; pair p = (2p, 2p + 1)
     float2 nx[GP_RP], ny[GP_RP], nz[GP_RP], mi[GP_RP], ax[GP_RP], ay[GP_RP], az[GP_RP], ap[GP_RP];
 #pragma unroll
     for (int p = 0; p < GP_RP; ++p) {
-        const int ia = I * GP_B + tid + (2 * p) * GP_THREADS, ib = ia + GP_THREADS;
-        const float4 a = ia < n ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = ib < n ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ka = tid + (2 * p) * GP_THREADS, kb = ka + GP_THREADS;
+        const int va = I * GP_B + ka, vb = I * GP_B + kb;
+        const int ia = va < ns ? global_of(va) : -1, ib = vb < ns ? global_of(vb) : -1;
+        if (BATCH) {
+            tidx[ka] = ia;
+            tidx[kb] = ib;
+        }
+        const float4 a = ia >= 0 ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = ib >= 0 ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
         nx[p] = make_float2(-a.x, -b.x);
         ny[p] = make_float2(-a.y, -b.y);
         nz[p] = make_float2(-a.z, -b.z);
@@ -263,8 +319,11 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, float eps2,
                 float v = 0.f;
 #pragma unroll
                 for (int w = 0; w < GP_WARPS; ++w) v = __fadd_rn(v, part[w * GP_SLAB * NC + q]);
-                const int j = J * GP_B + s0 + q / NC, comp = q % NC;
-                if (j < n)
+                const int comp = q % NC;
+                int j;
+                if (BATCH) j = sidx[s0 + q / NC];
+                else j = (J * GP_B + s0 + q / NC < n) ? J * GP_B + s0 + q / NC : -1;
+                if (j >= 0)
                     atomicAdd(&acc[(size_t)j * 4 + comp],
                               comp < 3 ? to_fixed(-v, sa1, sa2) : to_fixed(v, sp1, sp2));
             }
@@ -277,14 +336,23 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, float eps2,
     // the tile's sums of its targets
 #pragma unroll
     for (int p = 0; p < GP_RP; ++p) {
-        const int ia = I * GP_B + tid + (2 * p) * GP_THREADS, ib = ia + GP_THREADS;
-        if (ia < n) {
+        int ia, ib;
+        if (BATCH) {
+            ia = tidx[tid + (2 * p) * GP_THREADS];
+            ib = tidx[tid + (2 * p + 1) * GP_THREADS];
+        } else {
+            ia = I * GP_B + tid + (2 * p) * GP_THREADS;
+            ib = ia + GP_THREADS;
+            if (ia >= n) ia = -1;
+            if (ib >= n) ib = -1;
+        }
+        if (ia >= 0) {
             atomicAdd(&acc[(size_t)ia * 4 + 0], to_fixed(ax[p].x, sa1, sa2));
             atomicAdd(&acc[(size_t)ia * 4 + 1], to_fixed(ay[p].x, sa1, sa2));
             atomicAdd(&acc[(size_t)ia * 4 + 2], to_fixed(az[p].x, sa1, sa2));
             if (POT) atomicAdd(&acc[(size_t)ia * 4 + 3], to_fixed(ap[p].x, sp1, sp2));
         }
-        if (ib < n) {
+        if (ib >= 0) {
             atomicAdd(&acc[(size_t)ib * 4 + 0], to_fixed(ax[p].y, sa1, sa2));
             atomicAdd(&acc[(size_t)ib * 4 + 1], to_fixed(ay[p].y, sa1, sa2));
             atomicAdd(&acc[(size_t)ib * 4 + 2], to_fixed(az[p].y, sa1, sa2));
@@ -317,11 +385,63 @@ static int g_pairs_min_n = 65536;
 static std::mutex g_pairs_mutex;
 
 static void pairs_init() {
-    if (cudaFuncSetAttribute(pp_gravity_pairs_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) != cudaSuccess ||
-        cudaFuncSetAttribute(pp_gravity_pairs_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) != cudaSuccess)
-        g_pairs_status = SPH_ERR_CUDA;
+    const void *k[4] = {(const void *)pp_gravity_pairs_kernel<false, false>,
+                        (const void *)pp_gravity_pairs_kernel<true, false>,
+                        (const void *)pp_gravity_pairs_kernel<false, true>,
+                        (const void *)pp_gravity_pairs_kernel<true, true>};
+    for (const void *f : k)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) !=
+            cudaSuccess)
+            g_pairs_status = SPH_ERR_CUDA;
+}
+
+// The launches of one evaluation over n bodies: zero the scratch, the scale,
+// the tiles (one simulation: nb blocks in super-tile order; a batch: n_ctas
+// tiles described by sims / tile_off), then the fixed-point totals -> out.
+static int pairs_launch(const float4 *pos, int n, float G, float eps, float4 *out, int flags,
+                        void *d_work, int nb, const int4 *sims, const long long *tile_off,
+                        int n_sims, long long n_ctas, cudaStream_t st) {
+    std::call_once(g_pairs_once, pairs_init);
+    if (g_pairs_status != SPH_OK) return g_pairs_status;
+    int *flags_dev = gravity_flags_device();
+    if (!flags_dev) return SPH_ERR_CUDA;
+    if (n_ctas > 0x7fffffffll) return SPH_ERR_INVALID_ARG;
+    const bool pot = flags & SPH_GRAV_POTENTIAL;
+    const bool batch = sims != nullptr;
+    PairsHeader *hdr = static_cast<PairsHeader *>(d_work);
+    unsigned long long *acc =
+        reinterpret_cast<unsigned long long *>(static_cast<unsigned char *>(d_work) + kPairsAccOffset);
+    const float eps2 = eps * eps;
+    SPH_CUDA_TRY(cudaMemsetAsync(d_work, 0, pp_gravity_pairs_workspace_bytes(n), st));
+    pairs_mass_kernel<<<GP_MASS_BLOCKS, 256, 0, st>>>(pos, n, hdr);
+    pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr);
+    auto k = pot ? (batch ? pp_gravity_pairs_kernel<true, true> : pp_gravity_pairs_kernel<true, false>)
+                 : (batch ? pp_gravity_pairs_kernel<false, true> : pp_gravity_pairs_kernel<false, false>);
+    if (n_ctas > 0)
+        k<<<(unsigned)n_ctas, GP_THREADS, GP_SMEM, st>>>(pos, n, nb, sims, tile_off, n_sims, eps2,
+                                                        hdr, acc);
+    const long long *acc_s = reinterpret_cast<const long long *>(acc);
+    if (pot)
+        pairs_final_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
+    else
+        pairs_final_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
+    note_launch(n_ctas > 0 ? 4 : 3);
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+// Tiles of simulation s with ns bodies: nb_s (nb_s + 1) / 2, nb_s = ceil(ns / 2048).
+long long pairs_tiles(long long ns) {
+    const long long nb = (ns + GP_B - 1) / GP_B;
+    return nb * (nb + 1) / 2;
+}
+
+int launch_gravity_pairs_batched(const float4 *pos, int n, const int4 *d_sims,
+                                 const long long *d_tile_off, int n_sims, long long n_tiles,
+                                 float G, float eps, float4 *out, int flags, void *d_work,
+                                 cudaStream_t st) {
+    return pairs_launch(pos, n, G, eps, out, flags, d_work, 0, d_sims, d_tile_off, n_sims, n_tiles,
+                        st);
 }
 
 }  // namespace sphgb
@@ -366,35 +486,10 @@ extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float 
         (reinterpret_cast<uintptr_t>(d_acc_pot) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_work) & 255u))
         return SPH_ERR_INVALID_ARG;
-    std::call_once(g_pairs_once, pairs_init);
-    if (g_pairs_status != SPH_OK) return g_pairs_status;
-    int *flags_dev = gravity_flags_device();
-    if (!flags_dev) return SPH_ERR_CUDA;
     const long long nb = (n + GP_B - 1) / GP_B;
-    const long long n_tiles = nb * (nb + 1) / 2;
-    if (n_tiles > 0x7fffffffll) return SPH_ERR_INVALID_ARG;
-
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool pot = flags & SPH_GRAV_POTENTIAL;
-    const float4 *pos = reinterpret_cast<const float4 *>(d_pos_m);
-    PairsHeader *hdr = static_cast<PairsHeader *>(d_work);
-    unsigned long long *acc =
-        reinterpret_cast<unsigned long long *>(static_cast<unsigned char *>(d_work) + kPairsAccOffset);
-    const float eps2 = eps * eps;
-    SPH_CUDA_TRY(cudaMemsetAsync(d_work, 0, pp_gravity_pairs_workspace_bytes(n), st));
-    pairs_mass_kernel<<<GP_MASS_BLOCKS, 256, 0, st>>>(pos, n, hdr);
-    pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr);
-    if (pot)
-        pp_gravity_pairs_kernel<true><<<(unsigned)n_tiles, GP_THREADS, GP_SMEM, st>>>(pos, n, eps2, hdr, acc);
-    else
-        pp_gravity_pairs_kernel<false><<<(unsigned)n_tiles, GP_THREADS, GP_SMEM, st>>>(pos, n, eps2, hdr, acc);
-    const long long *acc_s = reinterpret_cast<const long long *>(acc);
-    float4 *out = reinterpret_cast<float4 *>(d_acc_pot);
-    if (pot)
-        pairs_final_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
-    else
-        pairs_final_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
-    note_launch(4);
-    SPH_LAUNCH_CHECK();
-    return SPH_OK;
+    const long long nsb = (nb + GP_SUPER - 1) / GP_SUPER;
+    const long long n_ctas = nsb * (nsb + 1) / 2 * GP_SUPER * GP_SUPER;
+    return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, G, eps,
+                        reinterpret_cast<float4 *>(d_acc_pot), flags, d_work, (int)nb, nullptr,
+                        nullptr, 1, n_ctas, (cudaStream_t)stream);
 }

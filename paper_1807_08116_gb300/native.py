@@ -131,6 +131,8 @@ def lib():
             "pp_gravity_pairs_workspace_bytes": (ctypes.c_size_t, [_I]),
             "pp_gravity_pairs_eligible": (_I, [_I, ctypes.c_float, _I]),
             "pp_gravity_pairs_min_n": (_I, [_I]),
+            "pp_gravity_pairs_batched": (_I, [_P, _P, ctypes.c_float, ctypes.c_float, _P, _I, _P,
+                                              ctypes.c_size_t, _P]),
             "sph_gravity_plan": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
             "sph_gravity_tune": (_I, [_I, _I]),
             "integrate_step": (_I, [_I, ctypes.c_double, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P,
@@ -533,6 +535,18 @@ def pp_gravity_batched(batch, pos_m, acc_pot, G=1.0, eps=0.01, flags=0, stream=N
                                   _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"), int(flags),
                                   _stream(stream))
     _check("pp_gravity_batched", rc)
+
+
+def pp_gravity_pairs_batched(batch, pos_m, acc_pot, work, G=1.0, eps=0.01, flags=0, stream=None):
+    """Pair-once gravity over every simulation of a batch (falls back to
+    pp_gravity_batched when not eligible or `work` is None / too small)."""
+    n = pos_m.shape[0]
+    wp, wb = (None, 0) if work is None else (work.data_ptr(), work.numel() * work.element_size())
+    rc = lib().pp_gravity_pairs_batched(batch.handle, _ptr(pos_m, torch.float32, (n, 4), "pos_m"),
+                                        float(G), float(eps),
+                                        _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"), int(flags),
+                                        wp, wb, _stream(stream))
+    _check("pp_gravity_pairs_batched", rc)
 
 
 def sph_ctx_set_batch(ctx, batch):

@@ -66,10 +66,8 @@ class Simulation:
         t["acc_hyd"] = torch.zeros((ng, 4), **f32)
         t["grav"] = torch.zeros((n, 4), **f32)
         self.grav_flags = int(grav_flags)
-        # scratch of the pair-once gravity kernel (single simulations; a batch
-        # uses the batched one-sided kernel)
-        if (pairs and batch_offsets is None and
-                nv.pp_gravity_pairs_eligible(n, self.params["eps"], self.grav_flags)):
+        # scratch of the pair-once gravity kernel (one simulation or a batch)
+        if pairs and nv.pp_gravity_pairs_eligible(n, self.params["eps"], self.grav_flags):
             t["grav_work"] = nv.pp_gravity_pairs_workspace(n, device=dev)
         self.t = t
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)

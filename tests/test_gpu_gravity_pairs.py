@@ -188,3 +188,86 @@ def test_simulation_takes_pair_path(orc):
     ref.step(1e-3)
     rv, _ = err(sim.velocities(), ref.velocities())
     assert rv < 1e-6
+
+
+def _batch_ics():
+    # uneven sizes across block boundaries, a gas-free and a dark-free one,
+    # and a 3-body simulation (one diagonal tile)
+    return [ics.two_halo(3000, 2500, seed=31), ics.single_halo(0, 1800, seed=32),
+            ics.single_halo(1300, 0, seed=33), ics.two_halo(700, 900, seed=34),
+            ics.single_halo(2, 1, seed=35)]
+
+
+def test_batched_matches_oracle_per_simulation(orc, low_threshold):
+    torch = need_gpu()
+    nv = low_threshold
+    from paper_1807_08116_gb300.sim import assemble_batch
+    lst = _batch_ics()
+    ic, go, do, so = assemble_batch(lst)
+    batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
+    pm = torch.as_tensor(pos_m_of(ic["r"], ic["m"]), device="cuda")
+    out = torch.full_like(pm, float("nan"))
+    work = nv.pp_gravity_pairs_workspace(pm.shape[0])
+    nv.pp_gravity_pairs_batched(batch, pm, out, work, flags=nv.SPH_GRAV_POTENTIAL)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    again = torch.full_like(pm, float("nan"))
+    nv.pp_gravity_pairs_batched(batch, pm, again, work, flags=nv.SPH_GRAV_POTENTIAL)
+    assert np.array_equal(again.cpu().numpy().astype(np.float64), got)   # reproducible
+    for s, d in enumerate(lst):
+        cols = np.concatenate([np.arange(go[s], go[s + 1]), ic["n_gas"] + np.arange(do[s], do[s + 1])])
+        acc, pot = orc.gravity(pos_m_of(d["r"], d["m"]))
+        rms, mx = err(got[cols, :3], acc)
+        assert rms <= RMS_TOL and mx <= MAX_TOL, (s, rms, mx)
+        prms, pmx = err(got[cols, 3:], pot[:, None])
+        assert prms <= RMS_TOL and pmx <= MAX_TOL, (s, prms, pmx)
+
+
+def test_batched_falls_back_without_scratch():
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.sim import assemble_batch
+    ic, go, do, so = assemble_batch(_batch_ics())
+    batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
+    pm = torch.as_tensor(pos_m_of(ic["r"], ic["m"]), device="cuda")
+    a, b = torch.empty_like(pm), torch.empty_like(pm)
+    nv.pp_gravity_pairs_batched(batch, pm, a, None)      # no scratch: the one-sided batch kernel
+    nv.pp_gravity_batched(batch, pm, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_batched_simulation_takes_pair_path(orc):
+    need_gpu()
+    from paper_1807_08116_gb300.sim import Simulation, assemble_batch
+    lst = [ics.two_halo(20000, 20000, seed=51), ics.single_halo(15000, 15000, seed=52)]
+    ic, go, do, so = assemble_batch(lst)
+    b = Simulation(ic, batch_offsets=(go, do, so))
+    assert "grav_work" in b.t
+    b.initial_rhs()
+    g = b.t["grav"].cpu().numpy().astype(np.float64)
+    for s, d in enumerate(lst):
+        cols = b.sim_slices(s)
+        rows = np.random.default_rng(s).choice(len(cols), 200, replace=False)
+        acc, _ = orc.gravity(pos_m_of(d["r"], d["m"]), rows=rows)
+        rms, mx = err(g[cols][rows, :3], acc)
+        assert rms <= RMS_TOL and mx <= MAX_TOL, (s, rms, mx)
+
+
+def test_batched_pair_path_graph_replay_equals_step():
+    torch = need_gpu()
+    from paper_1807_08116_gb300.sim import Simulation, assemble_batch
+    lst = [ics.two_halo(20000, 20000, seed=53), ics.single_halo(15000, 15000, seed=54)]
+    ic, go, do, so = assemble_batch(lst)
+    a = Simulation(ic, batch_offsets=(go, do, so))
+    b = Simulation(ic, batch_offsets=(go, do, so))
+    for sim in (a, b):
+        sim.initial_rhs()
+        sim.step(1e-3)
+    b.capture(1e-3)
+    for _ in range(2):
+        a.step(1e-3)
+        b.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(a.positions(), b.positions())
+    assert np.array_equal(a.velocities(), b.velocities())
