@@ -270,11 +270,12 @@ size_t pp_gravity_pairs_workspace_bytes(int32_t n);
 
 /* 1 if pp_gravity_pairs would use the pair-once kernel for n bodies: eps^2 > 0
  * in FP32, no SPH_GRAV_NO_KAHAN, no plan fixed by sph_gravity_tune, and
- * n >= the threshold of pp_gravity_pairs_min_n (default 65536). */
+ * n >= the threshold of pp_gravity_pairs_min_n (default 40960, where the
+ * pair-once kernel overtakes the one-sided one on GB300). */
 int pp_gravity_pairs_eligible(int32_t n, float eps, int32_t flags);
 
 /* Set the smallest n for which pp_gravity_pairs uses the pair-once kernel
- * (process-wide; 0 restores the default 65536). */
+ * (process-wide; 0 restores the default 40960). */
 int pp_gravity_pairs_min_n(int32_t n_min);
 
 /* Synchronise `stream`, read and clear the gravity kernel's device status

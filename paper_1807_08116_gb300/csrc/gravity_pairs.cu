@@ -381,7 +381,7 @@ __global__ void pairs_final_kernel(int n, float G, const PairsHeader *__restrict
 // ---------------------------------------------------------------------------
 static std::once_flag g_pairs_once;
 static int g_pairs_status = SPH_OK;
-static int g_pairs_min_n = 65536;
+static int g_pairs_min_n = 40960;   // measured crossover with the one-sided kernel
 static std::mutex g_pairs_mutex;
 
 static void pairs_init() {
@@ -456,7 +456,7 @@ extern "C" size_t pp_gravity_pairs_workspace_bytes(int32_t n) {
 extern "C" int pp_gravity_pairs_min_n(int32_t n_min) {
     if (n_min < 0) return SPH_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_pairs_mutex);
-    g_pairs_min_n = n_min ? n_min : 65536;
+    g_pairs_min_n = n_min ? n_min : 40960;
     return SPH_OK;
 }
 

@@ -50,8 +50,8 @@ def test_workspace_size_and_eligibility():
     from paper_1807_08116_gb300 import native as nv
     assert nv.pp_gravity_pairs_workspace_bytes(0) == 4096
     assert nv.pp_gravity_pairs_workspace_bytes(1000) == 4096 + 32 * 1000
-    assert nv.pp_gravity_pairs_eligible(65536, 0.01)
-    assert not nv.pp_gravity_pairs_eligible(65535, 0.01)
+    assert nv.pp_gravity_pairs_eligible(40960, 0.01)
+    assert not nv.pp_gravity_pairs_eligible(40959, 0.01)
     assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.0)            # unsoftened
     assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.01, nv.SPH_GRAV_NO_KAHAN)
     nv.sph_gravity_tune(4, 1)
