@@ -115,13 +115,16 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                     }
                     for (int j = s; j < e; ++j) {
                         if (j == i) continue;
-                        if (a.sim_s && a.sim_s[j] != si) continue;
                         const float4 q = a.pos_h_s[j];
+                        // the distance test first: most candidates fail it, and
+                        // the identity checks (same simulation, level and cell
+                        // as the probed one) are only needed for those that pass
+                        if (!nb_pred(p, q)) continue;
+                        if (a.sim_s && a.sim_s[j] != si) continue;
                         if (level_of(q.w, g.log2_L0, g.n_levels) != l) continue;
                         if (cell_of(q.x, g.x0, inv_c) != cx || cell_of(q.y, g.y0, inv_c) != cy ||
                             cell_of(q.z, g.z0, inv_c) != cz)
                             continue;
-                        if (!nb_pred(p, q)) continue;
                         if (FILL) {
                             long long w = base + cnt;
                             if (w < a.capacity) a.nb_idx[w] = j;
