@@ -259,8 +259,8 @@ int sph_gravity_tune(int32_t R, int32_t S);
  * reproducible whatever the order the tiles run in.
  * d_work (256-byte aligned, >= pp_gravity_pairs_workspace_bytes(n) bytes) is
  * caller-owned scratch, overwritten.  Runs pp_gravity instead when the call
- * is not eligible (pp_gravity_pairs_eligible) or the scratch is missing or
- * too small.  SPH_FLAG_GRAV_RANGE in the status word: the masses or eps put
+ * is not eligible (pp_gravity_pairs_eligible), the scratch is missing or too
+ * small, or n is above ~1.3e8 (more tiles than one grid can launch).  SPH_FLAG_GRAV_RANGE in the status word: the masses or eps put
  * the fixed-point scale outside 2^-250..2^250. */
 int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
                      int32_t flags, void *d_work, size_t work_bytes, sph_stream_t stream);

@@ -705,7 +705,7 @@ extern "C" int pp_gravity_pairs_batched(const sph_batch *b, const float *d_pos_m
     if (!b || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
     if (b->n == 0) return SPH_OK;
     if (!pp_gravity_pairs_eligible(b->n, eps, flags) || !d_work ||
-        work_bytes < pp_gravity_pairs_workspace_bytes(b->n))
+        work_bytes < pp_gravity_pairs_workspace_bytes(b->n) || b->n_pair_tiles > 0x7fffffffll)
         return pp_gravity_batched(b, d_pos_m, G, eps, d_acc_pot, flags, stream);
     if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot) ||
         (reinterpret_cast<uintptr_t>(d_work) & 255u))

@@ -489,6 +489,8 @@ extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float 
     const long long nb = (n + GP_B - 1) / GP_B;
     const long long nsb = (nb + GP_SUPER - 1) / GP_SUPER;
     const long long n_ctas = nsb * (nsb + 1) / 2 * GP_SUPER * GP_SUPER;
+    if (n_ctas > 0x7fffffffll)   // more than ~1.3e8 bodies: one CTA per tile no longer fits a grid
+        return pp_gravity(d_pos_m, n, G, eps, d_acc_pot, flags, stream);
     return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, G, eps,
                         reinterpret_cast<float4 *>(d_acc_pot), flags, d_work, (int)nb, nullptr,
                         nullptr, 1, n_ctas, (cudaStream_t)stream);
