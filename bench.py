@@ -401,7 +401,8 @@ def run_ensemble(args):
     """Batched ensemble: 64 independent two-halo collisions (total particles
     per simulation log-uniform in [8192, 262144], impact parameter U[0, 4a],
     speed U[0.5, 2] x escape) advanced (a) as one batch -- one launch per
-    stage, the step captured as a CUDA graph, autotuned gravity work units --
+    stage (gravity: the pair-once kernel over the tiles of every simulation),
+    the step captured as a CUDA graph --
     and (b) one simulation at a time with the single-simulation launches.
     Prints one JSON line with both aggregate particle-steps/s and the largest
     relative position difference between the two runs."""
