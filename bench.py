@@ -49,8 +49,8 @@ WORKLOAD_NAMES = {
 GFC_TRAFFIC = {
     "pp_gravity_kernel": {"file": "gravity.cu", "n": 4194304, "bytes": 870.39e6,
                           "sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721"},
-    "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 16.50e9,
-                                "sha256": "41d56d9002726f8a7bdc99b2cb7b34cbbb5542bd9ac75b7d4af59a9c4705acf4"},
+    "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 2.36e9,
+                                "sha256": "04afd4e73b1ff3c23e2702a087127879e7f53c42e53e33b106046276ae4a0d5a"},
 }
 # FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

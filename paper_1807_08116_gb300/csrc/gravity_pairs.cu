@@ -11,7 +11,7 @@
 // Layout of the work:
 //  * bodies are cut into blocks of B = 2048 (256 threads x 8 targets); the
 //    block pairs (I <= J) of the triangle are the tiles, one CTA each,
-//    visited in 16 x 16 super-tiles for L2 locality.  A
+//    visited in super-tiles of up to 128 x 128 for L2 locality.  A
 //    diagonal tile (I, I) is evaluated one-sided (every target against every
 //    source of the block, j = i left out of the potential); an off-diagonal
 //    tile evaluates each of its B x B pairs once.
@@ -86,21 +86,26 @@ __device__ __forceinline__ void tri_of(long long b, int &I, int &J) {
     I = (int)(b - (long long)j * (j + 1) / 2);
 }
 
-// CTA b -> tile (I, J).  Tiles are visited in super-tiles of 16 x 16 (the
-// super-tiles themselves in triangle order, the tiles inside row by row), so
-// the CTAs resident at one time touch about 16 target blocks and 16 source
-// blocks: their sources and the fixed-point sums they add to stay in L2.
+// CTA b -> tile (I, J).  Tiles are visited in super-tiles of S x S, S =
+// 2^lg (the super-tiles themselves in triangle order, the tiles inside row by
+// row), so the CTAs resident at one time touch a few target and source
+// blocks: their sources and the fixed-point sums they add to stay in L2, and
+// DRAM sees each block's sums about once per super-tile (2.6 GB per launch at
+// 4,194,304 bodies with S = 128, against 239 GB in plain triangle order).
 // Returns false for the cells of a super-tile below the diagonal or past the
 // last block (those CTAs exit at once).
-constexpr int GP_SUPER = 16;
-__device__ __forceinline__ bool tile_of(long long b, int nb, int &I, int &J) {
+__device__ __forceinline__ bool tile_of(long long b, int nb, int lg, int &I, int &J) {
     int P, Q;
-    tri_of(b / (GP_SUPER * GP_SUPER), P, Q);
-    const int local = (int)(b % (GP_SUPER * GP_SUPER));
-    I = P * GP_SUPER + local / GP_SUPER;
-    J = Q * GP_SUPER + local % GP_SUPER;
+    tri_of(b >> (2 * lg), P, Q);
+    const int local = (int)(b & ((1ll << (2 * lg)) - 1));
+    I = (P << lg) + (local >> lg);
+    J = (Q << lg) + (local & ((1 << lg) - 1));
     return I <= J && J < nb;
 }
+
+// log2 of the super-tile side for nb blocks: large enough to keep DRAM
+// traffic low, small enough that few CTAs fall on empty cells.
+inline int super_log2(long long nb) { return nb >= 1024 ? 7 : nb >= 256 ? 6 : 4; }
 
 // ---------------------------------------------------------------------------
 // Scale of the fixed-point sums.
@@ -245,7 +250,7 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
 // computes them (the shared-memory form cost 1.5% there).
 template <bool POT, bool BATCH>
 __global__ void __launch_bounds__(GP_THREADS, 1)
-pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb,
+pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
                         const int4 *__restrict__ sims, const long long *__restrict__ tile_off,
                         int n_sims, float eps2, const PairsHeader *__restrict__ hdr,
                         unsigned long long *__restrict__ acc) {
@@ -272,7 +277,7 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb,
         d0 = sd.z;
         ns = sd.y + sd.w;
         tri_of(b - tile_off[lo], I, J);
-    } else if (!tile_of(blockIdx.x, nb, I, J)) {
+    } else if (!tile_of(blockIdx.x, nb, lg, I, J)) {
         return;
     }
     auto global_of = [&](int v) { return v < ng ? g0 + v : d0 + (v - ng); };
@@ -418,8 +423,8 @@ static int pairs_launch(const float4 *pos, int n, float G, float eps, float4 *ou
     auto k = pot ? (batch ? pp_gravity_pairs_kernel<true, true> : pp_gravity_pairs_kernel<true, false>)
                  : (batch ? pp_gravity_pairs_kernel<false, true> : pp_gravity_pairs_kernel<false, false>);
     if (n_ctas > 0)
-        k<<<(unsigned)n_ctas, GP_THREADS, GP_SMEM, st>>>(pos, n, nb, sims, tile_off, n_sims, eps2,
-                                                        hdr, acc);
+        k<<<(unsigned)n_ctas, GP_THREADS, GP_SMEM, st>>>(pos, n, nb, super_log2(nb), sims, tile_off,
+                                                        n_sims, eps2, hdr, acc);
     const long long *acc_s = reinterpret_cast<const long long *>(acc);
     if (pot)
         pairs_final_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
@@ -487,8 +492,9 @@ extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float 
         (reinterpret_cast<uintptr_t>(d_work) & 255u))
         return SPH_ERR_INVALID_ARG;
     const long long nb = (n + GP_B - 1) / GP_B;
-    const long long nsb = (nb + GP_SUPER - 1) / GP_SUPER;
-    const long long n_ctas = nsb * (nsb + 1) / 2 * GP_SUPER * GP_SUPER;
+    const int lg = super_log2(nb);
+    const long long nsb = (nb + (1ll << lg) - 1) >> lg;
+    const long long n_ctas = (nsb * (nsb + 1) / 2) << (2 * lg);
     if (n_ctas > 0x7fffffffll)   // more than ~1.3e8 bodies: one CTA per tile no longer fits a grid
         return pp_gravity(d_pos_m, n, G, eps, d_acc_pot, flags, stream);
     return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, G, eps,
