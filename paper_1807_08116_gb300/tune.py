@@ -1,10 +1,13 @@
-"""Autotuning of the gravity launch plan by timing candidates on the device.
+"""Autotuning by timing candidates on the device.
 
-The single-simulation kernel has two knobs (R targets per thread, S CTAs
-per cluster sharing the source range); the batched kernel has R.  A built-in
-cost model picks a plan without timing; these functions time the candidates
-on the caller's own inputs instead and fix the fastest (sph_gravity_tune /
-sph_batch_set_plan), returning the measurements.
+Gravity has two kernels: the one-sided one, with two knobs (R targets per
+thread, S CTAs per cluster sharing the source range; the batched form has
+R), and the pair-once one, which wins once a launch has enough tiles to fill
+the GPU.  A built-in cost model and a measured default crossover choose
+without timing; these functions time the candidates instead and fix the
+fastest (sph_gravity_tune / sph_batch_set_plan / pp_gravity_pairs_min_n),
+returning the measurements.  tune_lanes does the same for the lanes per
+neighbour row of the SPH sums.
 """
 from __future__ import annotations
 
@@ -68,3 +71,34 @@ def tune_lanes(sim, reps=3):
     best = min(res, key=res.get)
     sim.set_lanes(best)
     return best, res
+
+
+def tune_pairs_threshold(make_pos_m, sizes=(16384, 24576, 32768, 40960, 49152, 65536),
+                         G=1.0, eps=0.01, reps=5, apply=True):
+    """Time the one-sided kernel (its cost-model plan) and the pair-once
+    kernel on make_pos_m(n) for each n in sizes (ascending); the smallest n
+    from which the pair-once kernel is faster at every larger size becomes
+    the threshold of pp_gravity_pairs_min_n (if apply).  Returns (threshold,
+    {n: (one_sided_ms, pairs_ms)}); threshold None if it never wins."""
+    res = {}
+    nv.pp_gravity_pairs_min_n(1)
+    try:
+        for n in sizes:
+            x = make_pos_m(n)
+            out = torch.empty_like(x)
+            work = nv.pp_gravity_pairs_workspace(n, device=x.device)
+            t1 = _time(lambda: nv.pp_gravity(x, out, G, eps), reps)
+            t2 = _time(lambda: nv.pp_gravity_pairs(x, out, work, G, eps), reps)
+            res[n] = (t1, t2)
+    finally:
+        nv.pp_gravity_pairs_min_n(0)
+    threshold = None
+    for n in sorted(res, reverse=True):
+        if res[n][1] < res[n][0]:
+            threshold = n
+        else:
+            break
+    if apply and threshold is not None:
+        nv.pp_gravity_pairs_min_n(threshold)
+    return threshold, res
+

@@ -271,3 +271,25 @@ def test_batched_pair_path_graph_replay_equals_step():
     torch.cuda.synchronize()
     assert np.array_equal(a.positions(), b.positions())
     assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_threshold_autotuner():
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.tune import tune_pairs_threshold
+
+    def make(n):
+        q = n // 4
+        d = ics.two_halo(q, q, seed=60)
+        return torch.as_tensor(pos_m_of(d["r"], d["m"]), device="cuda")
+    try:
+        thr, res = tune_pairs_threshold(make, sizes=(8192, 65536, 131072), reps=2)
+        assert set(res) == {8192, 65536, 131072}
+        # the timed crossover is applied, and the pair-once kernel wins at the top
+        assert res[131072][1] < res[131072][0]
+        assert thr is not None and thr <= 131072
+        assert nv.pp_gravity_pairs_eligible(thr, 0.01)
+        assert not nv.pp_gravity_pairs_eligible(thr - 1, 0.01)
+    finally:
+        nv.pp_gravity_pairs_min_n(0)
+    assert nv.pp_gravity_pairs_eligible(40960, 0.01)
