@@ -50,22 +50,30 @@ __device__ __forceinline__ int cell_of(float x, float x0, float inv_c) {
     return (int)u;
 }
 
-// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
-__device__ __forceinline__ unsigned long long spread3(unsigned v) {
-    unsigned long long x = v & 0x1fffffu;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
+// Spread the low 10 bits of v to every third bit of a 32-bit word (bit b ->
+// bit 3b).  The bucket keeps the low log2_M <= 30 bits of the full 63-bit
+// interleave plus the level salt; carries only move upwards, so those bits
+// depend only on the low 10 bits of each coordinate and 32-bit arithmetic
+// gives the same bucket as the 64-bit definition.
+constexpr unsigned kDilatedX = 0x09249249u;   // bits 0, 3, ..., 27
+__device__ __forceinline__ unsigned spread3_lo(unsigned v) {
+    unsigned x = v & 0x3ffu;
+    x = (x | (x << 16)) & 0xff0000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & kDilatedX;
     return x;
 }
 
+// spread3_lo(v + 1) from spread3_lo(v) (dilated-integer increment, mod 2^10).
+__device__ __forceinline__ unsigned spread3_next(unsigned d) { return ((d | ~kDilatedX) + 1u) & kDilatedX; }
+
+// Bucket of cell (cx, cy, cz) on level tag l: (interleave + l * kLevelSalt)
+// mod 2^log2_M, log2_M <= 30.
 __device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2_M) {
-    unsigned long long m = spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) |
-                           (spread3((unsigned)cz) << 2);
-    unsigned long long k = m + (unsigned long long)l * kLevelSalt;
-    return (int)(k & ((1ull << log2_M) - 1ull));
+    const unsigned m = spread3_lo((unsigned)cx) | (spread3_lo((unsigned)cy) << 1) |
+                       (spread3_lo((unsigned)cz) << 2);
+    return (int)((m + (unsigned)l * (unsigned)kLevelSalt) & ((1u << log2_M) - 1u));
 }
 
 // Occupancy bit of a super-cell (8 x 8 x 8 cells of one level): set by the
@@ -74,9 +82,10 @@ __device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2
 constexpr int kSuperShift = 3;
 constexpr unsigned long long kSuperSalt = 0xD1B54A32D192ED03ull;
 __device__ __forceinline__ unsigned super_bit(int sx, int sy, int sz, int l, int log2_B) {
-    unsigned long long m = spread3((unsigned)sx) | (spread3((unsigned)sy) << 1) |
-                           (spread3((unsigned)sz) << 2);
-    return (unsigned)((m + (unsigned long long)(l + 1) * kSuperSalt) & ((1ull << log2_B) - 1ull));
+    const unsigned m = spread3_lo((unsigned)sx) | (spread3_lo((unsigned)sy) << 1) |
+                       (spread3_lo((unsigned)sz) << 2);
+    const unsigned mask = log2_B >= 32 ? 0xffffffffu : ((1u << log2_B) - 1u);
+    return (m + (unsigned)(l + 1) * (unsigned)kSuperSalt) & mask;
 }
 
 // FP32 neighbour predicate: ((dx*dx + dy*dy) + dz*dz) < (h_i + h_j)^2,

@@ -99,13 +99,21 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
         const float mx = 9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f;
         const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
         const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
+        // bucket_of(cx, cy, cz, ...) with the interleave built per axis: z
+        // once per plane, y once per row, x stepped by a dilated increment
+        const unsigned salt = (unsigned)(l + kMaxLevels * si) * (unsigned)kLevelSalt;
+        const unsigned kmask = (1u << g.log2_M) - 1u;
+        const unsigned dlx = spread3_lo((unsigned)lx);
         for (int cz = lz; cz <= hz; ++cz) {
             const float dz = cell_gap(p.z, cz, csz, g.z0, mz);
+            const unsigned iz = spread3_lo((unsigned)cz) << 2;
             for (int cy = ly; cy <= hy; ++cy) {
                 const float dy = cell_gap(p.y, cy, csz, g.y0, my);
-                for (int cx = lx; cx <= hx; ++cx) {
+                const unsigned iyz = iz | (spread3_lo((unsigned)cy) << 1);
+                unsigned ix = dlx;
+                for (int cx = lx; cx <= hx; ++cx, ix = spread3_next(ix)) {
                     const float dx = cell_gap(p.x, cx, csz, g.x0, mx);
-                    const int k = bucket_of(cx, cy, cz, l + kMaxLevels * si, g.log2_M);
+                    const int k = (int)(((ix | iyz) + salt) & kmask);
                     const int s = a.cell_start[k], e = a.cell_start[k + 1];
                     if (s == e) continue;
                     {
@@ -113,9 +121,17 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (d2 > reach * reach * (1.0f + 3.0517578125e-05f)) continue;
                     }
-                    for (int j = s; j < e; ++j) {
-                        if (j == i) continue;
-                        const float4 q = a.pos_h_s[j];
+                    // candidates four at a time: their loads are issued together
+                    for (int j0 = s; j0 < e; j0 += 4) {
+                    float4 qb[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        qb[u] = j0 + u < e ? a.pos_h_s[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j0 + u;
+                        if (j >= e || j == i) continue;
+                        const float4 q = qb[u];
                         // the distance test first: most candidates fail it, and
                         // the identity checks (same simulation, level and cell
                         // as the probed one) are only needed for those that pass
@@ -141,6 +157,7 @@ __global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
                             if (l > li) atomicAdd(&a.rev[j], 1);
                         }
                         ++cnt;
+                    }
                     }
                 }
             }
