@@ -403,7 +403,8 @@ int pp_gravity_batched(const sph_batch *b, const float *d_pos_m, float G, float 
 
 /* pp_gravity_pairs for every simulation of the batch in one launch: the
  * tiles of all simulations' triangles, one CTA each, fixed-point sums over
- * the batch's n particles (scale from the whole batch's sum |m|).  d_work as
+ * the batch's n particles, each simulation with the scale of its own sum |m|
+ * (kept in the batch's workspace).  d_work as
  * for pp_gravity_pairs(b's n); runs pp_gravity_batched when not eligible
  * (pp_gravity_pairs_eligible on the batch's n) or d_work is missing / too
  * small. */

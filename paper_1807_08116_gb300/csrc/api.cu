@@ -92,6 +92,7 @@ struct sph_batch {
     const int *d_sim_of_gas;
     long long *d_tile_off;       // pair-once gravity: first tile of each simulation [n_sims + 1]
     long long n_pair_tiles;
+    void *d_pair_scales;         // pair-once gravity: fixed-point scale of each simulation
 };
 
 namespace {
@@ -583,7 +584,7 @@ size_t batch_units_cap(int n_sims, const int32_t *g, const int32_t *d) {
 }
 
 struct BatchCarve {
-    size_t sims, units, counter, tile_off, total;
+    size_t sims, units, counter, tile_off, scales, total;
 };
 
 BatchCarve batch_carve(int n_sims, size_t units_cap) {
@@ -593,7 +594,8 @@ BatchCarve batch_carve(int n_sims, size_t units_cap) {
     c.units = up(sizeof(int4) * (size_t)n_sims);
     c.counter = c.units + up(sizeof(int2) * units_cap);
     c.tile_off = c.counter + 256;
-    c.total = c.tile_off + up(sizeof(long long) * ((size_t)n_sims + 1));
+    c.scales = c.tile_off + up(sizeof(long long) * ((size_t)n_sims + 1));
+    c.total = c.scales + up(pairs_scale_bytes() * (size_t)n_sims);
     return c;
 }
 
@@ -654,6 +656,7 @@ extern "C" int sph_batch_create(int32_t n_sims, const int32_t *h_gas_off, const 
     b->units_cap = cap;
     b->d_sim_of_gas = d_sim_of_gas;
     b->d_tile_off = reinterpret_cast<long long *>(base + c.tile_off);
+    b->d_pair_scales = base + c.scales;
     std::vector<long long> tile_off(n_sims + 1, 0);
     for (int s = 0; s < n_sims; ++s)
         tile_off[s + 1] = tile_off[s] + pairs_tiles((long long)b->h_sims[s].y + b->h_sims[s].w);
@@ -710,8 +713,9 @@ extern "C" int pp_gravity_pairs_batched(const sph_batch *b, const float *d_pos_m
     if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot) ||
         (reinterpret_cast<uintptr_t>(d_work) & 255u))
         return SPH_ERR_INVALID_ARG;
-    return launch_gravity_pairs_batched(reinterpret_cast<const float4 *>(d_pos_m), b->n, b->d_sims,
-                                        b->d_tile_off, b->n_sims, b->n_pair_tiles, G, eps,
+    return launch_gravity_pairs_batched(reinterpret_cast<const float4 *>(d_pos_m), b->n, b->n_gas,
+                                        b->d_sims, b->d_tile_off, b->n_sims, b->n_pair_tiles,
+                                        b->d_pair_scales, G, eps,
                                         reinterpret_cast<float4 *>(d_acc_pot), flags, d_work,
                                         (cudaStream_t)stream);
 }

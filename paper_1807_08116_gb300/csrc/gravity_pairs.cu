@@ -64,13 +64,18 @@ constexpr int GP_SMEM = GP_SMEM_DUP + GP_SMEM_PART + GP_SMEM_IDX;
 static_assert(GP_SMEM <= 227 * 1024, "shared memory of the pair kernel");
 static_assert(GP_B % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
 
-// Start of the workspace; the fixed-point sums follow at kPairsAccOffset.
-struct PairsHeader {
-    int status;           // 1: the scale could not be placed (masses / eps out of range)
-    int pad0;
-    float s_acc1, s_acc2; // 2^-e_acc as two float factors
-    float s_pot1, s_pot2; // 2^-e_pot
+// Fixed-point scale of one simulation: sums of g are integers times 2^e_acc,
+// sums of phi integers times 2^e_pot.
+struct PairsScale {
+    float s_acc1, s_acc2;   // 2^-e_acc as two float factors
+    float s_pot1, s_pot2;   // 2^-e_pot
     double lsb_acc, lsb_pot;
+};
+
+// Start of the workspace; the fixed-point sums follow at kPairsAccOffset.
+// (A batch keeps one PairsScale per simulation in its own workspace.)
+struct PairsHeader {
+    PairsScale scale;
     double mass_part[GP_MASS_BLOCKS];
 };
 constexpr size_t kPairsAccOffset = 4096;
@@ -128,26 +133,38 @@ __global__ void pairs_mass_kernel(const float4 *__restrict__ pos, int n, PairsHe
 
 // Power-of-two scale 2^-e with the bound below 2^(e + 61), as two float
 // factors (each within the normal range for |e| <= 250) and as a double.
-__device__ void place_scale(double bound, float &s1, float &s2, double &lsb, int &status) {
+// Returns false if the bound is not finite or e falls outside that range.
+__device__ bool place_scale(double bound, float &s1, float &s2, double &lsb) {
+    bool ok = true;
     int e = 0;
     if (bound > 0.0 && bound <= 1.0e300) {
         int k;
         frexp(bound, &k);   // bound < 2^k
         e = k - 61;
     } else if (!(bound == 0.0)) {
-        status = 1;
+        ok = false;
     }
     if (e < -250 || e > 250) {
-        status = 1;
+        ok = false;
         e = 0;
     }
     const int e1 = -e / 2, e2 = -e - e1;
     s1 = ldexpf(1.0f, e1);
     s2 = ldexpf(1.0f, e2);
     lsb = ldexp(1.0, e);
+    return ok;
 }
 
-__global__ void pairs_scale_kernel(float eps, PairsHeader *__restrict__ h) {
+// Both scales from the sum M of |m| over the bodies that act on each other.
+// max over r of r / (r^2 + eps^2)^(3/2) is 2 / (3 sqrt 3 eps^2) < 0.385 / eps^2.
+__device__ void place_scales(double M, float eps, PairsScale &sc, int *flags) {
+    const double e = (double)eps;
+    const bool ok_a = place_scale(0.385 * M / (e * e), sc.s_acc1, sc.s_acc2, sc.lsb_acc);
+    const bool ok_p = place_scale(M / e, sc.s_pot1, sc.s_pot2, sc.lsb_pot);
+    if (!(ok_a && ok_p)) atomicOr(flags, SPH_FLAG_GRAV_RANGE);
+}
+
+__global__ void pairs_scale_kernel(float eps, PairsHeader *__restrict__ h, int *__restrict__ flags) {
     __shared__ double s[GP_MASS_BLOCKS];
     const int tid = threadIdx.x;
     s[tid] = h->mass_part[tid];
@@ -156,14 +173,28 @@ __global__ void pairs_scale_kernel(float eps, PairsHeader *__restrict__ h) {
         if (tid < w) s[tid] += s[tid + w];
         __syncthreads();
     }
-    if (tid == 0) {
-        const double M = s[0], e = (double)eps;
-        int status = 0;
-        // max over r of r / (r^2 + eps^2)^(3/2) is 2 / (3 sqrt 3 eps^2) < 0.385 / eps^2
-        place_scale(0.385 * M / (e * e), h->s_acc1, h->s_acc2, h->lsb_acc, status);
-        place_scale(M / e, h->s_pot1, h->s_pot2, h->lsb_pot, status);
-        h->status = status;
+    if (tid == 0) place_scales(s[0], eps, h->scale, flags);
+}
+
+// A batch: block s sums |m| over simulation s (gas range, then dark range,
+// fixed order) and places that simulation's scale, so each simulation keeps
+// the resolution of its own mass and unit scale.
+__global__ void pairs_batch_scale_kernel(const float4 *__restrict__ pos, const int4 *__restrict__ sims,
+                                         float eps, PairsScale *__restrict__ scales,
+                                         int *__restrict__ flags) {
+    __shared__ double s[256];
+    const int tid = threadIdx.x;
+    const int4 sd = sims[blockIdx.x];   // (g0, ng, d0, nd)
+    double v = 0.0;
+    for (int q = tid; q < sd.y; q += 256) v += fabs((double)pos[sd.x + q].w);
+    for (int q = tid; q < sd.w; q += 256) v += fabs((double)pos[sd.z + q].w);
+    s[tid] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) s[tid] += s[tid + w];
+        __syncthreads();
     }
+    if (tid == 0) place_scales(s[0], eps, scales[blockIdx.x], flags);
 }
 
 __device__ __forceinline__ unsigned long long to_fixed(float v, float s1, float s2) {
@@ -252,7 +283,7 @@ template <bool POT, bool BATCH>
 __global__ void __launch_bounds__(GP_THREADS, 1)
 pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
                         const int4 *__restrict__ sims, const long long *__restrict__ tile_off,
-                        int n_sims, float eps2, const PairsHeader *__restrict__ hdr,
+                        int n_sims, float eps2, const PairsScale *__restrict__ scales,
                         unsigned long long *__restrict__ acc) {
     constexpr int NC = POT ? 4 : 3;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -262,7 +293,7 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
     int *sidx = reinterpret_cast<int *>(smem + GP_SMEM_DUP + GP_SMEM_PART);  // [GP_B] sources
     int *tidx = sidx + GP_B;                                               // [GP_B] targets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int I, J, g0 = 0, ng = n, d0 = 0, ns = n;
+    int I, J, g0 = 0, ng = n, d0 = 0, ns = n, sim = 0;
     if (BATCH) {
         const long long b = blockIdx.x;
         int lo = 0, hi = n_sims - 1;   // last simulation whose first tile is <= b
@@ -271,6 +302,7 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
             if (tile_off[mid] <= b) lo = mid;
             else hi = mid - 1;
         }
+        sim = lo;
         const int4 sd = sims[lo];
         g0 = sd.x;
         ng = sd.y;
@@ -312,7 +344,8 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
         mi[p] = make_float2(a.w, b.w);
         ax[p] = ay[p] = az[p] = ap[p] = make_float2(0.f, 0.f);
     }
-    const float sa1 = hdr->s_acc1, sa2 = hdr->s_acc2, sp1 = hdr->s_pot1, sp2 = hdr->s_pot2;
+    const PairsScale sc = scales[sim];
+    const float sa1 = sc.s_acc1, sa2 = sc.s_acc2, sp1 = sc.s_pot1, sp2 = sc.s_pot2;
     __syncthreads();
     const float2 e2 = make_float2(eps2, eps2);
     float *wpart = part + warp * GP_SLAB * NC;
@@ -366,17 +399,30 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
     }
 }
 
-// Fixed-point totals -> float4 (gx, gy, gz, phi).
-template <bool POT>
-__global__ void pairs_final_kernel(int n, float G, const PairsHeader *__restrict__ hdr,
-                                   const long long *__restrict__ acc, float4 *__restrict__ out,
-                                   int *__restrict__ flags) {
+// Fixed-point totals -> float4 (gx, gy, gz, phi).  BATCH: body i takes the
+// scale of its simulation (the last one whose gas / dark range starts at or
+// before i).
+template <bool POT, bool BATCH>
+__global__ void pairs_final_kernel(int n, int n_gas, float G, const PairsScale *__restrict__ scales,
+                                   const int4 *__restrict__ sims, int n_sims,
+                                   const long long *__restrict__ acc, float4 *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && hdr->status) atomicOr(flags, SPH_FLAG_GRAV_RANGE);
     if (i >= n) return;
-    const double la = hdr->lsb_acc * (double)G;
+    int sim = 0;
+    if (BATCH) {
+        const bool gas = i < n_gas;
+        int lo = 0, hi = n_sims - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((gas ? sims[mid].x : sims[mid].z) <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        sim = lo;
+    }
+    const PairsScale sc = scales[sim];
+    const double la = sc.lsb_acc * (double)G;
     const long long *a = acc + (size_t)i * 4;
-    const float phi = POT ? (float)(-(double)G * (double)a[3] * hdr->lsb_pot) : 0.f;
+    const float phi = POT ? (float)(-(double)G * (double)a[3] * sc.lsb_pot) : 0.f;
     out[i] = make_float4((float)((double)a[0] * la), (float)((double)a[1] * la),
                          (float)((double)a[2] * la), phi);
 }
@@ -403,9 +449,10 @@ static void pairs_init() {
 // The launches of one evaluation over n bodies: zero the scratch, the scale,
 // the tiles (one simulation: nb blocks in super-tile order; a batch: n_ctas
 // tiles described by sims / tile_off), then the fixed-point totals -> out.
-static int pairs_launch(const float4 *pos, int n, float G, float eps, float4 *out, int flags,
-                        void *d_work, int nb, const int4 *sims, const long long *tile_off,
-                        int n_sims, long long n_ctas, cudaStream_t st) {
+static int pairs_launch(const float4 *pos, int n, int n_gas, float G, float eps, float4 *out,
+                        int flags, void *d_work, int nb, const int4 *sims,
+                        const long long *tile_off, int n_sims, long long n_ctas,
+                        PairsScale *batch_scales, cudaStream_t st) {
     std::call_once(g_pairs_once, pairs_init);
     if (g_pairs_status != SPH_OK) return g_pairs_status;
     int *flags_dev = gravity_flags_device();
@@ -418,22 +465,30 @@ static int pairs_launch(const float4 *pos, int n, float G, float eps, float4 *ou
         reinterpret_cast<unsigned long long *>(static_cast<unsigned char *>(d_work) + kPairsAccOffset);
     const float eps2 = eps * eps;
     SPH_CUDA_TRY(cudaMemsetAsync(d_work, 0, pp_gravity_pairs_workspace_bytes(n), st));
-    pairs_mass_kernel<<<GP_MASS_BLOCKS, 256, 0, st>>>(pos, n, hdr);
-    pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr);
+    const PairsScale *scales;
+    if (batch) {
+        pairs_batch_scale_kernel<<<n_sims, 256, 0, st>>>(pos, sims, eps, batch_scales, flags_dev);
+        scales = batch_scales;
+    } else {
+        pairs_mass_kernel<<<GP_MASS_BLOCKS, 256, 0, st>>>(pos, n, hdr);
+        pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr, flags_dev);
+        scales = &hdr->scale;
+    }
     auto k = pot ? (batch ? pp_gravity_pairs_kernel<true, true> : pp_gravity_pairs_kernel<true, false>)
                  : (batch ? pp_gravity_pairs_kernel<false, true> : pp_gravity_pairs_kernel<false, false>);
     if (n_ctas > 0)
         k<<<(unsigned)n_ctas, GP_THREADS, GP_SMEM, st>>>(pos, n, nb, super_log2(nb), sims, tile_off,
-                                                        n_sims, eps2, hdr, acc);
+                                                        n_sims, eps2, scales, acc);
     const long long *acc_s = reinterpret_cast<const long long *>(acc);
-    if (pot)
-        pairs_final_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
-    else
-        pairs_final_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(n, G, hdr, acc_s, out, flags_dev);
-    note_launch(n_ctas > 0 ? 4 : 3);
+    auto f = pot ? (batch ? pairs_final_kernel<true, true> : pairs_final_kernel<true, false>)
+                 : (batch ? pairs_final_kernel<false, true> : pairs_final_kernel<false, false>);
+    f<<<(n + 255) / 256, 256, 0, st>>>(n, n_gas, G, scales, sims, n_sims, acc_s, out);
+    note_launch((n_ctas > 0 ? 3 : 2) + (batch ? 0 : 1));
     SPH_LAUNCH_CHECK();
     return SPH_OK;
 }
+
+size_t pairs_scale_bytes() { return sizeof(PairsScale); }
 
 // Tiles of simulation s with ns bodies: nb_s (nb_s + 1) / 2, nb_s = ceil(ns / 2048).
 long long pairs_tiles(long long ns) {
@@ -441,12 +496,12 @@ long long pairs_tiles(long long ns) {
     return nb * (nb + 1) / 2;
 }
 
-int launch_gravity_pairs_batched(const float4 *pos, int n, const int4 *d_sims,
+int launch_gravity_pairs_batched(const float4 *pos, int n, int n_gas, const int4 *d_sims,
                                  const long long *d_tile_off, int n_sims, long long n_tiles,
-                                 float G, float eps, float4 *out, int flags, void *d_work,
-                                 cudaStream_t st) {
-    return pairs_launch(pos, n, G, eps, out, flags, d_work, 0, d_sims, d_tile_off, n_sims, n_tiles,
-                        st);
+                                 void *d_scales, float G, float eps, float4 *out, int flags,
+                                 void *d_work, cudaStream_t st) {
+    return pairs_launch(pos, n, n_gas, G, eps, out, flags, d_work, 0, d_sims, d_tile_off, n_sims,
+                        n_tiles, static_cast<PairsScale *>(d_scales), st);
 }
 
 }  // namespace sphgb
@@ -497,7 +552,7 @@ extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float 
     const long long n_ctas = (nsb * (nsb + 1) / 2) << (2 * lg);
     if (n_ctas > 0x7fffffffll)   // more than ~1.3e8 bodies: one CTA per tile no longer fits a grid
         return pp_gravity(d_pos_m, n, G, eps, d_acc_pot, flags, stream);
-    return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, G, eps,
+    return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, n, G, eps,
                         reinterpret_cast<float4 *>(d_acc_pot), flags, d_work, (int)nb, nullptr,
-                        nullptr, 1, n_ctas, (cudaStream_t)stream);
+                        nullptr, 1, n_ctas, nullptr, (cudaStream_t)stream);
 }

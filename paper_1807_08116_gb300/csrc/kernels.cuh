@@ -31,10 +31,11 @@ int gravity_num_sms();
 // gravity_pairs.cu: tiles of one simulation with ns bodies, and the pair-once
 // evaluation of a batch (sims (g0, ng, d0, nd), tile_off[n_sims + 1])
 long long pairs_tiles(long long ns);
-int launch_gravity_pairs_batched(const float4 *pos, int n, const int4 *d_sims,
+size_t pairs_scale_bytes();   // bytes of one simulation's fixed-point scale
+int launch_gravity_pairs_batched(const float4 *pos, int n, int n_gas, const int4 *d_sims,
                                  const long long *d_tile_off, int n_sims, long long n_tiles,
-                                 float G, float eps, float4 *out, int flags, void *d_work,
-                                 cudaStream_t st);
+                                 void *d_scales, float G, float eps, float4 *out, int flags,
+                                 void *d_work, cudaStream_t st);
 // device address of the gravity kernels' status word (SPH_FLAG_*)
 int *gravity_flags_device();
 // true while sph_gravity_tune has fixed a one-sided launch plan

@@ -293,3 +293,31 @@ def test_threshold_autotuner():
     finally:
         nv.pp_gravity_pairs_min_n(0)
     assert nv.pp_gravity_pairs_eligible(40960, 0.01)
+
+
+def test_batched_scale_per_simulation(orc, low_threshold):
+    # simulations of very different mass (and unit) scales in one batch: each
+    # keeps the fixed-point resolution of its own sum |m|
+    torch = need_gpu()
+    nv = low_threshold
+    from paper_1807_08116_gb300.sim import assemble_batch
+    a = ics.two_halo(3000, 2500, seed=61)
+    b = ics.single_halo(1300, 900, seed=62)
+    b = dict(b, m=b["m"] * 1e-10, r=b["r"] * 1e-3)
+    lst = [a, b]
+    ic, go, do, so = assemble_batch(lst)
+    batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
+    pm = torch.as_tensor(pos_m_of(ic["r"], ic["m"]), device="cuda")
+    out = torch.full_like(pm, float("nan"))
+    nv.pp_gravity_pairs_batched(batch, pm, out, nv.pp_gravity_pairs_workspace(pm.shape[0]),
+                                eps=1e-5, flags=nv.SPH_GRAV_POTENTIAL)
+    torch.cuda.synchronize()
+    assert nv.pp_gravity_status() == 0
+    got = out.cpu().numpy().astype(np.float64)
+    for s, d in enumerate(lst):
+        cols = np.concatenate([np.arange(go[s], go[s + 1]), ic["n_gas"] + np.arange(do[s], do[s + 1])])
+        acc, pot = orc.gravity(pos_m_of(d["r"], d["m"]), eps=1e-5)
+        rms, mx = err(got[cols, :3], acc)
+        assert rms <= RMS_TOL and mx <= MAX_TOL, (s, rms, mx)
+        prms, pmx = err(got[cols, 3:], pot[:, None])
+        assert prms <= RMS_TOL and pmx <= MAX_TOL, (s, prms, pmx)
