@@ -223,6 +223,16 @@ int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d
                const float *d_mass, const float *d_acc_hyd, const float *d_grav, float C_cfl,
                float *d_dt_particle, float *d_dt_min, sph_stream_t stream);
 
+/* sph_forces with the time step of Eq. 17 taken in the same pass over the
+ * neighbour lists: writes d_acc_dedt as sph_forces does, and min(dt_max,
+ * min_i dt_i) to *d_dt_min (dt_i as for sph_cfl_dt, from the acceleration
+ * this pass computes plus d_grav at the same positions; bitwise the value
+ * sph_cfl_dt gives for that acceleration).  d_dt_particle optional.
+ * C_cfl > 0, dt_max > 0. */
+int sph_forces_cfl(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+                   const float *d_mass, float *d_acc_dedt, const float *d_grav, float C_cfl,
+                   float dt_max, float *d_dt_particle, float *d_dt_min, sph_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Stage GFC: direct particle-particle gravity (Eq. 4).                      */
 /* ------------------------------------------------------------------------ */
@@ -354,6 +364,17 @@ int sph_rhs_initial(sph_ctx *ctx, SphState *st, sph_stream_t stream);
  * `stream` before and after stage s (SPH_STAGE_*; a skipped stage records
  * both back to back). */
 int sph_step(sph_ctx *ctx, SphState *st, double dt, sph_stream_t stream);
+
+/* One step of sph_step with an adaptive size chosen on the device: the first
+ * HFC (at r, v, e, with the gravity of the previous step) also evaluates
+ * Eq. 17 and writes dt = min(dt_max, min_i dt_i) to the device float *d_dt,
+ * which both leapfrog phases read; no host round trip, so the step can be
+ * captured in a CUDA graph.  Right after sph_rhs_initial only the time step
+ * is evaluated (the forces are current).  Needs gas (n_gas >= 1); with a
+ * batch attached the step is the smallest over all its simulations.  On
+ * return *d_dt holds the step just taken. */
+int sph_step_cfl(sph_ctx *ctx, SphState *st, float C_cfl, float dt_max, float *d_dt,
+                 sph_stream_t stream);
 
 /* FP64 reductions of one state in a fixed order (deterministic) by one
  * thread block: d_out[8] (device) = {kinetic sum m v^2 / 2, thermal

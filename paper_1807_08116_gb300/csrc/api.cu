@@ -3,6 +3,7 @@
 // whole-step driver that sequences them as the paper's predictor-corrector
 // flow (Sect. 2.2 and the kernel list of Sect. 3).
 #include <algorithm>
+#include <limits>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -436,7 +437,31 @@ extern "C" int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, con
     return launch_cfl(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start, ctx->nb_idx,
                       (int)ctx->capacity, n_gas, hp, C_cfl,
                       reinterpret_cast<const float4 *>(d_acc_hyd),
-                      reinterpret_cast<const float4 *>(d_grav), d_dt_particle, d_dt_min, st);
+                      reinterpret_cast<const float4 *>(d_grav), d_dt_particle, d_dt_min,
+                      std::numeric_limits<float>::infinity(), st);
+}
+
+extern "C" int sph_forces_cfl(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
+                              const float *d_mass, float *d_acc_dedt, const float *d_grav,
+                              float C_cfl, float dt_max, float *d_dt_particle, float *d_dt_min,
+                              sph_stream_t stream) {
+    if (!ctx || n_gas != ctx->n_sorted || !ctx->nb_built || !d_dt_min || !(C_cfl > 0.0f) ||
+        !(dt_max > 0.0f))
+        return SPH_ERR_INVALID_ARG;
+    if (n_gas > 0 && (!d_vel_e || !d_rho || !d_mass || !d_acc_dedt || !d_grav ||
+                      !aligned16(d_vel_e) || !aligned16(d_acc_dedt) || !aligned16(d_grav)))
+        return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    HydroParams hp = hydro_params(ctx);
+    int rc;
+    if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
+        return rc;
+    return launch_forces(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
+                         ctx->nb_idx, (int)ctx->capacity, n_gas, hp, ctx->hydro_lanes,
+                         reinterpret_cast<float4 *>(d_acc_dedt), st,
+                         reinterpret_cast<const float4 *>(d_grav), C_cfl, d_dt_particle, d_dt_min,
+                         dt_max);
 }
 
 // ---------------------------------------------------------------------------
@@ -557,6 +582,47 @@ extern "C" int sph_step(sph_ctx *ctx, SphState *s, double dt, sph_stream_t strea
               integrate_step(SPH_CORRECT, dt, s->n, s->n_gas, s->r, s->v, s->e, s->v_save,
                              s->e_save, s->acc_hyd, s->grav, s->mass, s->h, nullptr, nullptr,
                              s->vel_e, stream));
+    s->fresh = 0;
+    return SPH_OK;
+}
+
+extern "C" int sph_step_cfl(sph_ctx *ctx, SphState *s, float C_cfl, float dt_max, float *d_dt,
+                            sph_stream_t stream) {
+    if (!state_ok(ctx, s) || !ctx || s->n_gas < 1 || !d_dt || !(C_cfl > 0.0f) || !(dt_max > 0.0f))
+        return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const StageMark mark{s->events, st};
+    int rc;
+    // HFC at (r_n, v_n, e_n) with the time step of Eq. 17 in the same pass
+    // (right after sph_rhs_initial the forces are current: only the step)
+    if (s->fresh) {
+        HydroParams hp = hydro_params(ctx);
+        SPH_STAGE(SPH_STAGE_HFC_PRED,
+                  launch_cfl(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
+                             ctx->nb_idx, (int)ctx->capacity, s->n_gas, hp, C_cfl,
+                             reinterpret_cast<const float4 *>(s->acc_hyd),
+                             reinterpret_cast<const float4 *>(s->grav), nullptr, d_dt, dt_max, st));
+    } else {
+        SPH_STAGE(SPH_STAGE_HFC_PRED,
+                  sph_forces_cfl(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, s->grav,
+                                 C_cfl, dt_max, nullptr, d_dt, stream));
+    }
+    // the rest of the step as in sph_step, with the step size read on the device
+    SPH_STAGE(SPH_STAGE_SU_PRED,
+              integrate_launch(SPH_PREDICT, 0.0, d_dt, s->n, s->n_gas, s->r, s->v, s->e, s->v_save,
+                               s->e_save, s->acc_hyd, s->grav, s->mass, s->h, s->pos_m, s->pos_h,
+                               s->vel_e, stream));
+    SPH_STAGE(SPH_STAGE_SP, sph_bin_and_sort(ctx, s->pos_h, s->n_gas, nullptr, nullptr, nullptr,
+                                             nullptr, stream));
+    SPH_STAGE(SPH_STAGE_NB, sph_build_neighbors(ctx, s->n_gas, nullptr, nullptr, 0, nullptr, stream));
+    SPH_STAGE(SPH_STAGE_DC, sph_density(ctx, s->n_gas, s->mass, s->rho, s->h, stream));
+    SPH_STAGE(SPH_STAGE_GFC, gravity_of(ctx, s, stream));
+    SPH_STAGE(SPH_STAGE_HFC_CORR,
+              sph_forces(ctx, s->n_gas, s->vel_e, s->rho, s->mass, s->acc_hyd, stream));
+    SPH_STAGE(SPH_STAGE_SU_CORR,
+              integrate_launch(SPH_CORRECT, 0.0, d_dt, s->n, s->n_gas, s->r, s->v, s->e, s->v_save,
+                               s->e_save, s->acc_hyd, s->grav, s->mass, s->h, nullptr, nullptr,
+                               s->vel_e, stream));
     s->fresh = 0;
     return SPH_OK;
 }

@@ -7,6 +7,8 @@
 // to the caller's order through perm.  The working set of a row's
 // neighbours (16-48 bytes each) is read through L1/L2; the lists themselves
 // stream from HBM.
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -35,6 +37,40 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask) {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_min(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, o));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o));
+    return v;
+}
+
+// Time step of Eq. 17 for one gas particle from its neighbour extrema
+// (s^min the smallest |r_ij|, c^max the largest c_ij, mu^max the largest
+// |mu_ij|) and its total acceleration Q = a_hyd + g and heating E.
+__device__ __forceinline__ float cfl_bound(float C, const HydroParams &hp, float s_min, float c_max,
+                                           float mu_max, float4 a, float4 g) {
+    const float qx = a.x + g.x, qy = a.y + g.y, qz = a.z + g.z;
+    const float qn = sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+    const float den = c_max * (1.0f + 1.2f * hp.alpha) + 1.2f * hp.beta * mu_max +
+                      sqrtf(s_min * (qn + fabsf(a.w)));
+    return C * s_min / den;
+}
+
+// Minimum over the warp of a non-negative time step, one atomic per warp
+// (non-negative floats order like their bit patterns).
+__device__ __forceinline__ void warp_dt_min(float dt, unsigned *dt_min_bits) {
+    float m = dt;
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m >= 0.0f) atomicMin(dt_min_bits, __float_as_uint(m));
 }
 
 // Density of Eq. 7: G lanes share one sorted row; lane q takes neighbours
@@ -107,25 +143,37 @@ __global__ void hydro_prep_kernel(const float4 *__restrict__ vel_e, const float 
 }
 
 // Hydrodynamic acceleration and heating of Eqs. 10-11, G lanes per row.
-template <int G>
+// CFL: the same pass also takes the neighbour extrema of Eq. 17 and, once the
+// row's acceleration is summed, writes the particle's time step (dt_out,
+// optional) and lowers *dt_min_bits to the smallest one; grav is the gravity
+// at the same positions.
+template <int G, bool CFL>
 __global__ void __launch_bounds__(128)
 forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
               const float4 *__restrict__ aux_s, const int *__restrict__ perm,
               const int *__restrict__ nb_start, const int *__restrict__ nb_idx, int cap, int n,
-              HydroParams hp, float4 *__restrict__ acc_out) {
+              HydroParams hp, float4 *__restrict__ acc_out, const float4 *__restrict__ grav,
+              float C, float *__restrict__ dt_out, unsigned *__restrict__ dt_min_bits) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / G, q = t % G;
-    if (i >= n) return;
+    const bool valid = i < n;
+    if (!CFL && !valid) return;   // with CFL every lane takes part in the warp minimum
     const unsigned mask = group_mask<G>();
-    const float4 p = pos_h_s[i];
-    const float4 v = vel_s[i];
-    const float4 ai = aux_s[i];
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p, ai = p;
+    int b = 0, e = 0;
+    if (valid) {
+        p = pos_h_s[i];
+        v = vel_s[i];
+        ai = aux_s[i];
+        // rows are clipped to the list capacity (an overflowed build is flagged)
+        e = min(nb_start[i + 1], cap);
+        b = min(nb_start[i], e);
+    }
     // dW_p/dxi = -(45 / (64 pi)) h^-3 (2 - xi)^2  (derivative of Eq. 9)
     const float kdw = -45.0f / 64.0f * kInvPi;
     Kahan ax, ay, az, de;
     ax.init(); ay.init(); az.init(); de.init();
-    // rows are clipped to the list capacity (an overflowed build is flagged)
-    const int e = min(nb_start[i + 1], cap), b = min(nb_start[i], e);
+    float s2_min = __int_as_float(0x7f800000), c_max = 0.0f, mu_max = 0.0f;
 #pragma unroll 4
     for (int k = b + q; k < e; k += G) {
         const int j = nb_idx[k];
@@ -143,12 +191,17 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
         // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
         const float f = r > 0.0f ? kdw * (ih * ih * ih) * tt * tt * ih / r : 0.0f;
         const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+        const float c_ij = 0.5f * (ai.w + aj.w);
         float nu = 0.0f;
         if (rv < 0.0f) {
             const float mu = hij * rv / fmaf(hp.eta * hij, hij, r2);
             const float rho_ij = 0.5f * (ai.y + aj.y);
-            const float c_ij = 0.5f * (ai.w + aj.w);
             nu = mu * fmaf(hp.beta, mu, -hp.alpha * c_ij) / rho_ij;
+            if (CFL) mu_max = fmaxf(mu_max, -mu);
+        }
+        if (CFL) {
+            s2_min = fminf(s2_min, r2);
+            c_max = fmaxf(c_max, c_ij);
         }
         const float Pi = ai.z + aj.z + nu;
         const float g = aj.x * Pi * f;   // m_j Pi_ij f
@@ -161,7 +214,22 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
     const float sy = group_sum<G>(ay.s - ay.c, mask);
     const float sz = group_sum<G>(az.s - az.c, mask);
     const float se = group_sum<G>(de.s - de.c, mask);
-    if (q == 0) acc_out[perm[i]] = make_float4(sx, sy, sz, se);
+    if (!CFL) {
+        if (q == 0) acc_out[perm[i]] = make_float4(sx, sy, sz, se);
+        return;
+    }
+    s2_min = group_min<G>(s2_min, mask);
+    c_max = group_max<G>(c_max, mask);
+    mu_max = group_max<G>(mu_max, mask);
+    float dt = __int_as_float(0x7f800000);   // +inf: no bound
+    if (valid && q == 0) {
+        const int oi = perm[i];
+        const float4 a = make_float4(sx, sy, sz, se);
+        acc_out[oi] = a;
+        if (e > b) dt = cfl_bound(C, hp, sqrtf(s2_min), c_max, mu_max, a, grav[oi]);
+        if (dt_out) dt_out[oi] = dt;
+    }
+    warp_dt_min(dt, dt_min_bits);
 }
 
 // Time step of Eq. 17 per gas particle, and its minimum.  mu^max is the
@@ -199,14 +267,7 @@ cfl_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
             }
         }
         const int oi = perm[i];
-        if (e > b) {
-            const float4 a = acc_hyd[oi], g = grav[oi];
-            const float qx = a.x + g.x, qy = a.y + g.y, qz = a.z + g.z;
-            const float qn = sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
-            const float den = c_max * (1.0f + 1.2f * hp.alpha) + 1.2f * hp.beta * mu_max +
-                              sqrtf(s_min * (qn + fabsf(a.w)));
-            dt = C * s_min / den;
-        }
+        if (e > b) dt = cfl_bound(C, hp, s_min, c_max, mu_max, acc_hyd[oi], grav[oi]);
         if (dt_out) dt_out[oi] = dt;
     }
     // block minimum, then one atomic per block (dt >= 0: the bits order like the values)
@@ -221,6 +282,12 @@ cfl_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
     }
 }
 
+static unsigned host_float_bits(float x) {
+    unsigned u;
+    std::memcpy(&u, &x, sizeof(u));
+    return u;
+}
+
 __global__ void fill_u32_kernel(unsigned *p, unsigned v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
 }
@@ -228,8 +295,8 @@ __global__ void fill_u32_kernel(unsigned *p, unsigned v) {
 int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, const int *perm,
                const int *nb_start, const int *nb_idx, int cap, int n, HydroParams hp, float C,
                const float4 *acc_hyd, const float4 *grav, float *dt_out, float *dt_min,
-               cudaStream_t st) {
-    fill_u32_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned *>(dt_min), 0x7f800000u);
+               float dt_cap, cudaStream_t st) {
+    fill_u32_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned *>(dt_min), host_float_bits(dt_cap));
     note_launch();
     if (n > 0) {
         cfl_kernel<<<(n + 127) / 128, 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx,
@@ -274,15 +341,32 @@ int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, 
 
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st) {
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st,
+                  const float4 *grav, float C, float *dt_out, float *dt_min, float dt_cap) {
+    const bool cfl = dt_min != nullptr;
+    unsigned *bits = reinterpret_cast<unsigned *>(dt_min);
+    if (cfl) {
+        fill_u32_kernel<<<1, 32, 0, st>>>(bits, host_float_bits(dt_cap));
+        note_launch();
+    }
     if (n > 0) {
         const long long T = (long long)n * lanes;
+#define SPHGB_FORCES(G)                                                                         \
+    if (cfl)                                                                                    \
+        forces_kernel<G, true><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, \
+                                                            nb_idx, cap, n, hp, acc_out, grav, C, \
+                                                            dt_out, bits);                      \
+    else                                                                                        \
+        forces_kernel<G, false><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, \
+                                                             nb_idx, cap, n, hp, acc_out, nullptr, \
+                                                             0.0f, nullptr, nullptr)
         switch (lanes) {
-            case 1: forces_kernel<1><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
-            case 2: forces_kernel<2><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
-            case 8: forces_kernel<8><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
-            default: forces_kernel<4><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, nb_idx, cap, n, hp, acc_out); break;
+            case 1: SPHGB_FORCES(1); break;
+            case 2: SPHGB_FORCES(2); break;
+            case 8: SPHGB_FORCES(8); break;
+            default: SPHGB_FORCES(4); break;
         }
+#undef SPHGB_FORCES
         note_launch();
     }
     SPH_LAUNCH_CHECK();

@@ -11,7 +11,8 @@
 
 namespace sphgb {
 
-__global__ void integrate_kernel(int phase, double dt, int n, int n_gas, double *__restrict__ r,
+__global__ void integrate_kernel(int phase, double dt_arg, const float *__restrict__ d_dt, int n,
+                                 int n_gas, double *__restrict__ r,
                                  double *__restrict__ v, double *__restrict__ e,
                                  double *__restrict__ v_save, double *__restrict__ e_save,
                                  const float4 *__restrict__ acc_hyd,
@@ -21,6 +22,9 @@ __global__ void integrate_kernel(int phase, double dt, int n, int n_gas, double 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool gas = i < n_gas;
+    // the step size comes from the host, or from device memory (a time step
+    // chosen on the device by the CFL condition, Eq. 17)
+    const double dt = d_dt ? (double)*d_dt : dt_arg;
     const double half_dt = __dmul_rn(0.5, dt);
     if (phase != SPH_EMIT) {
         const float4 g = grav[i];
@@ -96,15 +100,13 @@ diagnostics_kernel(int n, int n_gas, const double *__restrict__ v, const double 
     if (threadIdx.x == 7) out[7] = 0.0;
 }
 
-}  // namespace sphgb
-
-using namespace sphgb;
-
-extern "C" int integrate_step(int32_t phase, double dt, int32_t n, int32_t n_gas, double *d_r,
-                              double *d_v, double *d_e, double *d_v_save, double *d_e_save,
-                              const float *d_acc_hyd, const float *d_grav, const float *d_mass,
-                              const float *d_h, float *d_pos_m, float *d_pos_h, float *d_vel_e,
-                              sph_stream_t stream) {
+// integrate_step with the step size optionally read from device memory
+// (d_dt != NULL: one float, e.g. written by the CFL epilogue of the forces).
+int integrate_launch(int phase, double dt, const float *d_dt, int n, int n_gas, double *d_r,
+                     double *d_v, double *d_e, double *d_v_save, double *d_e_save,
+                     const float *d_acc_hyd, const float *d_grav, const float *d_mass,
+                     const float *d_h, float *d_pos_m, float *d_pos_h, float *d_vel_e,
+                     sph_stream_t stream) {
     if (phase < SPH_PREDICT || phase > SPH_EMIT || n < 0 || n_gas < 0 || n_gas > n)
         return SPH_ERR_INVALID_ARG;
     if (n == 0) return SPH_OK;
@@ -117,13 +119,26 @@ extern "C" int integrate_step(int32_t phase, double dt, int32_t n, int32_t n_gas
     if (d_pos_m && !d_mass) return SPH_ERR_INVALID_ARG;
     if (n_gas > 0 && d_pos_h && !d_h) return SPH_ERR_INVALID_ARG;
     integrate_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-        phase, dt, n, n_gas, d_r, d_v, d_e, d_v_save, d_e_save,
+        phase, dt, d_dt, n, n_gas, d_r, d_v, d_e, d_v_save, d_e_save,
         reinterpret_cast<const float4 *>(d_acc_hyd), reinterpret_cast<const float4 *>(d_grav),
         d_mass, d_h, reinterpret_cast<float4 *>(d_pos_m), reinterpret_cast<float4 *>(d_pos_h),
         reinterpret_cast<float4 *>(d_vel_e));
     note_launch();
     SPH_LAUNCH_CHECK();
     return SPH_OK;
+}
+
+}  // namespace sphgb
+
+using namespace sphgb;
+
+extern "C" int integrate_step(int32_t phase, double dt, int32_t n, int32_t n_gas, double *d_r,
+                              double *d_v, double *d_e, double *d_v_save, double *d_e_save,
+                              const float *d_acc_hyd, const float *d_grav, const float *d_mass,
+                              const float *d_h, float *d_pos_m, float *d_pos_h, float *d_vel_e,
+                              sph_stream_t stream) {
+    return integrate_launch(phase, dt, nullptr, n, n_gas, d_r, d_v, d_e, d_v_save, d_e_save,
+                            d_acc_hyd, d_grav, d_mass, d_h, d_pos_m, d_pos_h, d_vel_e, stream);
 }
 
 extern "C" int sph_diagnostics(const SphState *st, double *d_out, sph_stream_t stream) {

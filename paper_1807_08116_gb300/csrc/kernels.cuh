@@ -77,12 +77,23 @@ int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, co
                    float *rho_out, float *h_next_out, float *mass_s, cudaStream_t st);
 int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
                       int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st);
+// integrate.cu: integrate_step with the step size optionally read from
+// device memory (d_dt != NULL)
+int integrate_launch(int phase, double dt, const float *d_dt, int n, int n_gas, double *d_r,
+                     double *d_v, double *d_e, double *d_v_save, double *d_e_save,
+                     const float *d_acc_hyd, const float *d_grav, const float *d_mass,
+                     const float *d_h, float *d_pos_m, float *d_pos_h, float *d_vel_e,
+                     sph_stream_t stream);
 int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, const int *perm,
                const int *nb_start, const int *nb_idx, int cap, int n, HydroParams hp, float C,
                const float4 *acc_hyd, const float4 *grav, float *dt_out, float *dt_min,
-               cudaStream_t st);
+               float dt_cap, cudaStream_t st);
+// dt_min != NULL: also the CFL time step of Eq. 17 in the same pass (grav at
+// the same positions; *dt_min = min(dt_cap, smallest particle step))
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st);
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st,
+                  const float4 *grav = nullptr, float C = 0.0f, float *dt_out = nullptr,
+                  float *dt_min = nullptr, float dt_cap = 0.0f);
 
 }  // namespace sphgb

@@ -139,6 +139,10 @@ def lib():
                                     _P, _P, _P, _P]),
             "sph_rhs_initial": (_I, [_P, ctypes.POINTER(SphState), _P]),
             "sph_step": (_I, [_P, ctypes.POINTER(SphState), ctypes.c_double, _P]),
+            "sph_step_cfl": (_I, [_P, ctypes.POINTER(SphState), ctypes.c_float, ctypes.c_float, _P,
+                                  _P]),
+            "sph_forces_cfl": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P,
+                                    _P, _P]),
             "sph_diagnostics": (_I, [ctypes.POINTER(SphState), _P, _P]),
             "sph_events_create": (_I, [_I, _P]),
             "sph_events_destroy": (_I, [_I, _P]),
@@ -476,6 +480,28 @@ def sph_rhs_initial(ctx, state: SphState, stream=None):
 def sph_step(ctx, state: SphState, dt, stream=None):
     _check("sph_step", lib().sph_step(ctx.handle if ctx else None, ctypes.byref(state), float(dt),
                                       _stream(stream)))
+
+
+def sph_step_cfl(ctx, state: SphState, C, dt_max, dt_out, stream=None):
+    """One step whose size (Eq. 17, capped at dt_max) is chosen on the device
+    and written to dt_out (a 1-element float32 CUDA tensor)."""
+    _check("sph_step_cfl", lib().sph_step_cfl(ctx.handle if ctx else None, ctypes.byref(state),
+                                              float(C), float(dt_max),
+                                              _ptr(dt_out, torch.float32, (1,), "dt_out"),
+                                              _stream(stream)))
+
+
+def sph_forces_cfl(ctx, n_gas, vel_e, rho, mass, acc_dedt, grav, C, dt_max, dt_min,
+                   dt_particle=None, stream=None):
+    """sph_forces plus the Eq. 17 time step in the same pass."""
+    f32 = torch.float32
+    rc = lib().sph_forces_cfl(ctx.handle, int(n_gas), _ptr(vel_e, f32, (n_gas, 4), "vel_e"),
+                              _ptr(rho, f32, (n_gas,), "rho"), _ptr(mass, f32, (n_gas,), "mass"),
+                              _ptr(acc_dedt, f32, (n_gas, 4), "acc_dedt"),
+                              _ptr(grav, f32, None, "grav"), float(C), float(dt_max),
+                              _ptr(dt_particle, f32, (n_gas,), "dt_particle", True),
+                              _ptr(dt_min, f32, (1,), "dt_min"), _stream(stream))
+    _check("sph_forces_cfl", rc)
 
 
 def sph_diagnostics(state: SphState, out, stream=None):

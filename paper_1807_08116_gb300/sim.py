@@ -149,6 +149,17 @@ class Simulation:
         if check:
             self._check_capacity()
 
+    def step_cfl(self, C=0.5, dt_max=1e-2, check=True):
+        """One step whose size min(dt_max, Eq. 17) is chosen on the device in
+        the step's first force pass; returns the 1-element device tensor that
+        holds it (no host round trip unless read)."""
+        if not hasattr(self, "dt_used"):
+            self.dt_used = torch.zeros(1, dtype=torch.float32, device=self.device)
+        nv.sph_step_cfl(self.ctx, self.state, C, dt_max, self.dt_used)
+        if check:
+            self._check_capacity()
+        return self.dt_used
+
     # -- CUDA graph of one step --------------------------------------------------
     def capture(self, dt):
         """Capture one step (launch sequence of sph_step) into a CUDA graph.
@@ -161,12 +172,24 @@ class Simulation:
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             with torch.cuda.graph(g, stream=side):
-                nv.sph_step(self.ctx, self.state, dt, stream=side)
+                if dt is None:   # adaptive: (C, dt_max) in self.graph_cfl
+                    C, dt_max = self.graph_cfl
+                    nv.sph_step_cfl(self.ctx, self.state, C, dt_max, self.dt_used, stream=side)
+                else:
+                    nv.sph_step(self.ctx, self.state, dt, stream=side)
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         self.graph = g
         self.graph_dt = dt
         return g
+
+    def capture_cfl(self, C=0.5, dt_max=1e-2):
+        """Capture one adaptive step (sph_step_cfl); each replay chooses its
+        own step size on the device and leaves it in self.dt_used."""
+        if not hasattr(self, "dt_used"):
+            self.dt_used = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.graph_cfl = (C, dt_max)
+        return self.capture(None)
 
     def replay(self, check=True):
         """One step by replaying the captured graph (re-captured if the
