@@ -50,7 +50,7 @@ GFC_TRAFFIC = {
     "pp_gravity_kernel": {"file": "gravity.cu", "n": 4194304, "bytes": 870.39e6,
                           "sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721"},
     "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 2.36e9,
-                                "sha256": "a516fd7062b7abb52d382216814c61198452954b54d7acd8417baf9ec416b138"},
+                                "sha256": "7856f687d519e8bd524fc7a0057e59076cd21455c0140eb822863879d9005990"},
 }
 # FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -28,10 +28,10 @@
 //    are converted to 64-bit fixed-point integers and added with integer
 //    atomics.  Integer addition is exact and associative, so the result does
 //    not depend on the order in which the CTAs run: it is bitwise
-//    reproducible.  The scale is fixed per launch from a bound on |g|:
-//    sum_j |m_j| max_r r / (r^2 + eps^2)^(3/2) = sum_j |m_j| 2 / (3 sqrt(3)
-//    eps^2), computed on the device in FP64 by a fixed-order reduction, and
-//    placed 2^61 below the int64 limit.  Values below 2^-61 of that bound are
+//    reproducible.  The scale is fixed per launch (per simulation in a batch)
+//    from a bound on |g|: sum_j |m_j| max_r r / (r^2 + eps^2)^(3/2) =
+//    sum_j |m_j| 2 / (3 sqrt(3) eps^2), computed on the device in FP64 by a
+//    fixed-order reduction, and placed 2^61 below the int64 limit.  Values below 2^-61 of that bound are
 //    rounded away (an absolute error far below the FP32 rounding of any
 //    acceleration that is not ~10^10 times smaller than the largest possible
 //    one).
@@ -95,7 +95,7 @@ __device__ __forceinline__ void tri_of(long long b, int &I, int &J) {
 // 2^lg (the super-tiles themselves in triangle order, the tiles inside row by
 // row), so the CTAs resident at one time touch a few target and source
 // blocks: their sources and the fixed-point sums they add to stay in L2, and
-// DRAM sees each block's sums about once per super-tile (2.6 GB per launch at
+// DRAM sees each block's sums about once per super-tile (2.4 GB per launch at
 // 4,194,304 bodies with S = 128, against 239 GB in plain triangle order).
 // Returns false for the cells of a super-tile below the diagonal or past the
 // last block (those CTAs exit at once).
