@@ -262,7 +262,7 @@ int sph_gravity_tune(int32_t R, int32_t S);
 
 /* The same g_i (and phi_i) as pp_gravity with every unordered pair evaluated
  * once (Newton's third law: one inverse cube serves both bodies, 16 instead
- * of 2 x 12 FP32 operations per pair).  Bodies are cut into blocks of 2048;
+ * of 2 x 12 FP32 operations per pair).  Bodies are cut into blocks of 1024;
  * each tile of block pairs (I <= J) is one CTA, and the per-tile partial
  * sums are accumulated exactly as 64-bit fixed-point integers whose scale is
  * set per launch from sum |m_j| and eps, so the result is bitwise
@@ -280,12 +280,12 @@ size_t pp_gravity_pairs_workspace_bytes(int32_t n);
 
 /* 1 if pp_gravity_pairs would use the pair-once kernel for n bodies: eps^2 > 0
  * in FP32, no SPH_GRAV_NO_KAHAN, no plan fixed by sph_gravity_tune, and
- * n >= the threshold of pp_gravity_pairs_min_n (default 40960, where the
+ * n >= the threshold of pp_gravity_pairs_min_n (default 16384, where the
  * pair-once kernel overtakes the one-sided one on GB300). */
 int pp_gravity_pairs_eligible(int32_t n, float eps, int32_t flags);
 
 /* Set the smallest n for which pp_gravity_pairs uses the pair-once kernel
- * (process-wide; 0 restores the default 40960). */
+ * (process-wide; 0 restores the default 16384). */
 int pp_gravity_pairs_min_n(int32_t n_min);
 
 /* Synchronise `stream`, read and clear the gravity kernel's device status

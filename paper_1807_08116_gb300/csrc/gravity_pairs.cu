@@ -9,14 +9,16 @@
 // one-sided interactions.
 //
 // Layout of the work:
-//  * bodies are cut into blocks of B = 2048 (256 threads x 8 targets); the
-//    block pairs (I <= J) of the triangle are the tiles, one CTA each,
-//    visited in super-tiles of up to 128 x 128 for L2 locality.  A
+//  * bodies are cut into blocks of B = 1024 (128 threads x 8 targets); the
+//    block pairs (I <= J) of the triangle are the tiles, one CTA each (four
+//    resident per SM), visited in super-tiles of up to 256 x 256 for L2
+//    locality.  (Blocks of 2048 with 256 threads were 0.4-14% slower, most
+//    at 16-64 K bodies where they gave too few tiles to fill the GPU.)  A
 //    diagonal tile (I, I) is evaluated one-sided (every target against every
 //    source of the block, j = i left out of the potential); an off-diagonal
 //    tile evaluates each of its B x B pairs once.
-//  * a CTA keeps its 2048 targets (block I) in registers, two per packed
-//    FP32x2 operation, and its 2048 sources (block J) in shared memory,
+//  * a CTA keeps its 1024 targets (block I) in registers, two per packed
+//    FP32x2 operation, and its 1024 sources (block J) in shared memory,
 //    expanded to (x, x, y, y), (z, z, m, m) so that each operand of a packed
 //    operation comes from one 16-byte load.
 //  * inside a warp, the 32 lanes hold different targets; in step t lane l
@@ -50,7 +52,7 @@
 
 namespace sphgb {
 
-constexpr int GP_THREADS = 256;
+constexpr int GP_THREADS = 128;
 constexpr int GP_RP = 4;                      // target pairs per thread
 constexpr int GP_R = 2 * GP_RP;               // targets per thread
 constexpr int GP_B = GP_THREADS * GP_R;       // bodies per block
@@ -95,8 +97,8 @@ __device__ __forceinline__ void tri_of(long long b, int &I, int &J) {
 // 2^lg (the super-tiles themselves in triangle order, the tiles inside row by
 // row), so the CTAs resident at one time touch a few target and source
 // blocks: their sources and the fixed-point sums they add to stay in L2, and
-// DRAM sees each block's sums about once per super-tile (2.4 GB per launch at
-// 4,194,304 bodies with S = 128, against 239 GB in plain triangle order).
+// DRAM sees each block's sums about once per super-tile (a few GB per launch
+// at 4,194,304 bodies, against 239 GB in plain triangle order).
 // Returns false for the cells of a super-tile below the diagonal or past the
 // last block (those CTAs exit at once).
 __device__ __forceinline__ bool tile_of(long long b, int nb, int lg, int &I, int &J) {
@@ -110,7 +112,7 @@ __device__ __forceinline__ bool tile_of(long long b, int nb, int lg, int &I, int
 
 // log2 of the super-tile side for nb blocks: large enough to keep DRAM
 // traffic low, small enough that few CTAs fall on empty cells.
-inline int super_log2(long long nb) { return nb >= 1024 ? 7 : nb >= 256 ? 6 : 4; }
+inline int super_log2(long long nb) { return nb >= 4096 ? 8 : nb >= 1024 ? 7 : nb >= 256 ? 6 : 4; }
 
 // ---------------------------------------------------------------------------
 // Scale of the fixed-point sums.
@@ -432,7 +434,7 @@ __global__ void pairs_final_kernel(int n, int n_gas, float G, const PairsScale *
 // ---------------------------------------------------------------------------
 static std::once_flag g_pairs_once;
 static int g_pairs_status = SPH_OK;
-static int g_pairs_min_n = 40960;   // measured crossover with the one-sided kernel
+static int g_pairs_min_n = 16384;   // measured crossover with the one-sided kernel
 static std::mutex g_pairs_mutex;
 
 static void pairs_init() {
@@ -516,7 +518,7 @@ extern "C" size_t pp_gravity_pairs_workspace_bytes(int32_t n) {
 extern "C" int pp_gravity_pairs_min_n(int32_t n_min) {
     if (n_min < 0) return SPH_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_pairs_mutex);
-    g_pairs_min_n = n_min ? n_min : 40960;
+    g_pairs_min_n = n_min ? n_min : 16384;
     return SPH_OK;
 }
 

@@ -73,7 +73,7 @@ def tune_lanes(sim, reps=3):
     return best, res
 
 
-def tune_pairs_threshold(make_pos_m, sizes=(16384, 24576, 32768, 40960, 49152, 65536),
+def tune_pairs_threshold(make_pos_m, sizes=(8192, 12288, 16384, 24576, 32768, 49152, 65536),
                          G=1.0, eps=0.01, reps=5, apply=True):
     """Time the one-sided kernel (its cost-model plan) and the pair-once
     kernel on make_pos_m(n) for each n in sizes (ascending); the smallest n

@@ -48,14 +48,20 @@ def test_batched_gravity_is_bitwise_per_simulation():
     assert nv.pp_gravity_status() == 0
 
 
-def test_batched_steps_match_separate_runs(orc):
+@pytest.mark.parametrize("pairs", [False, True])
+def test_batched_steps_match_separate_runs(orc, pairs):
+    # pairs=False: the batch and the lone runs use the one-sided gravity
+    # kernels and agree to 1e-7; pairs=True: the batch (17,300 bodies) takes
+    # the pair-once kernel while the lone runs stay one-sided, so they agree
+    # to the force tolerance
     need_gpu()
     from paper_1807_08116_gb300.sim import Simulation, assemble_batch
     lst = _ics()[:4]
     ic, go, do, so = assemble_batch(lst)
-    b = Simulation(ic, batch_offsets=(go, do, so))
+    b = Simulation(ic, batch_offsets=(go, do, so), pairs=pairs)
+    assert ("grav_work" in b.t) == pairs
     b.initial_rhs()
-    singles = [Simulation(d) for d in lst]
+    singles = [Simulation(d, pairs=False) for d in lst]
     for s in singles:
         s.initial_rhs()
     for _ in range(3):
@@ -67,7 +73,7 @@ def test_batched_steps_match_separate_runs(orc):
         cols = b.sim_slices(s)
         assert np.abs(rb[cols] - sim.positions()).max() < 1e-10
         rv, mv = err(vb[cols], sim.velocities())
-        assert rv < 1e-7, (s, rv)
+        assert rv < (1e-6 if pairs else 1e-7), (s, rv)
     # and the batch against the FP64 oracle on the largest simulation
     d = lst[0]
     ref = orc.OracleSim(d["r"].T, d["v"].T, d["e"], d["m"], d["h"], d["n_gas"])

@@ -50,8 +50,8 @@ def test_workspace_size_and_eligibility():
     from paper_1807_08116_gb300 import native as nv
     assert nv.pp_gravity_pairs_workspace_bytes(0) == 4096
     assert nv.pp_gravity_pairs_workspace_bytes(1000) == 4096 + 32 * 1000
-    assert nv.pp_gravity_pairs_eligible(40960, 0.01)
-    assert not nv.pp_gravity_pairs_eligible(40959, 0.01)
+    assert nv.pp_gravity_pairs_eligible(16384, 0.01)
+    assert not nv.pp_gravity_pairs_eligible(16383, 0.01)
     assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.0)            # unsoftened
     assert not nv.pp_gravity_pairs_eligible(1 << 20, 0.01, nv.SPH_GRAV_NO_KAHAN)
     nv.sph_gravity_tune(4, 1)
@@ -61,9 +61,9 @@ def test_workspace_size_and_eligibility():
         nv.sph_gravity_tune(0)
 
 
-@pytest.mark.parametrize("n", [1, 2, 33, 2047, 2048, 2049, 4096, 5000, 9999])
+@pytest.mark.parametrize("n", [1, 2, 33, 1023, 1024, 1025, 2048, 2049, 5000, 9999])
 def test_ragged_block_counts(orc, low_threshold, n):
-    # 1 block (diagonal tile only) up to 5 blocks with a ragged last block
+    # 1 block (diagonal tile only) up to 10 blocks with a ragged last block
     nv = low_threshold
     rng = np.random.default_rng(n)
     pm = pos_m_of(rng.normal(size=(n, 3)), rng.uniform(0.5, 1.5, n) / n)
@@ -283,8 +283,8 @@ def test_threshold_autotuner():
         d = ics.two_halo(q, q, seed=60)
         return torch.as_tensor(pos_m_of(d["r"], d["m"]), device="cuda")
     try:
-        thr, res = tune_pairs_threshold(make, sizes=(8192, 65536, 131072), reps=2)
-        assert set(res) == {8192, 65536, 131072}
+        thr, res = tune_pairs_threshold(make, sizes=(4096, 65536, 131072), reps=2)
+        assert set(res) == {4096, 65536, 131072}
         # the timed crossover is applied, and the pair-once kernel wins at the top
         assert res[131072][1] < res[131072][0]
         assert thr is not None and thr <= 131072
@@ -292,7 +292,7 @@ def test_threshold_autotuner():
         assert not nv.pp_gravity_pairs_eligible(thr - 1, 0.01)
     finally:
         nv.pp_gravity_pairs_min_n(0)
-    assert nv.pp_gravity_pairs_eligible(40960, 0.01)
+    assert nv.pp_gravity_pairs_eligible(16384, 0.01)
 
 
 def test_batched_scale_per_simulation(orc, low_threshold):
