@@ -87,6 +87,41 @@ def gfc_traffic(n, kernel="pp_gravity_kernel"):
     return rec["bytes"] if digest == rec["sha256"] else None
 
 
+# Algorithmic DRAM bytes of the SPH and sort stages per unit (the minimal
+# traffic of each stage's data): sort (bin, scan, scatter, gather) 150 B and
+# density 300 B per gas particle, each force pass 330 B per gas particle,
+# each leapfrog phase 180 B per particle; the neighbour lists 4 B per entry
+# plus 4 B per row start.
+STAGE_BYTES = {"sp": ("gas", 150.0), "dc": ("gas", 300.0), "hfc_pred": ("gas", 330.0),
+               "hfc_corr": ("gas", 330.0), "su_pred": ("all", 180.0), "su_corr": ("all", 180.0)}
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    """Measured copy bandwidth of this GPU (GB/s) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (no measured peak on this machine)"
+
+
+def stage_roofline(stage_ms, n, ng, nb_entries):
+    """Achieved GB/s of each HBM-bound stage: algorithmic bytes / stage time."""
+    peak, note = hbm_peak()
+    out = {"peak_gbs": peak, "peak_note": note}
+    for k, (unit, b) in STAGE_BYTES.items():
+        if k in stage_ms and stage_ms[k] > 0:
+            byts = b * (ng if unit == "gas" else n)
+            gbs = byts / (stage_ms[k] / 1e3) / 1e9
+            out[k] = {"bytes": byts, "gbs": gbs, "frac": gbs / peak}
+    if nb_entries is not None and stage_ms.get("nb", 0) > 0:
+        byts = 4.0 * nb_entries + 4.0 * (ng + 1)
+        gbs = byts / (stage_ms["nb"] / 1e3) / 1e9
+        out["nb"] = {"bytes": byts, "gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 # FP32-pipe operations per ordered interaction: the one-sided kernel does
 # 3 FADD + 3 FFMA + 3 FMUL + 3 FFMA (+1 MUFU); the pair-once kernel does 16
 # per unordered pair (3 FADD, 3 FFMA, 4 FMUL, 2 x 3 FFMA), i.e. 8 per
@@ -298,6 +333,7 @@ def run_ours(args):
     flags = sim.ctx.device_status() if sim.ctx is not None else 0
     if flags:
         raise RuntimeError(f"device status flags {flags} during the timed steps")
+    nb_entries = sim.ctx.nb_total() if (sim.ctx is not None and ng > 0) else None
     ms = t_start.elapsed_time(t_stop)
     stage = {name: float(np.mean([e.stage_ms()[name] for e in evs])) for name in nv.STAGES}
     for e in evs:
@@ -360,6 +396,7 @@ def run_ours(args):
                        "precision": "FP32 forces (Kahan), FP64 leapfrog state"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "stage_ms": stage,
+            "stage_roofline": stage_roofline(stage, n, ng, nb_entries),
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
