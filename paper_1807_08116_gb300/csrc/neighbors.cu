@@ -18,6 +18,26 @@
 // distinct cells through the hash; each candidate is accepted only if its own
 // level and cell equal the probed ones, so no pair is counted twice.
 // Rows are [own part in search order | reverse part sorted ascending].
+//
+// The walk is warp-cooperative.  A warp takes 32 consecutive sorted rows
+// (neighbours in space, since the sort is by cell) and splits them into
+// groups: a leader row and every other pending row of the same simulation
+// and level whose cell lies within kNbGroupReach cells of the leader's on
+// that level.  A group walks the union of its members' search boxes with
+// warp-uniform loops, 32 cells at a time: lane t reads the bucket of cell
+// c0 + t, so one round trip covers 32 probes, and a cell is kept when it
+// passes the cell-distance cut of some member.  The candidates of the kept
+// cells are numbered in cell order and loaded 32 at a time (one per lane),
+// their level, cell and simulation are checked once by the lane that loaded
+// them, and the survivors are broadcast from shared memory to every member,
+// which applies the FP32 predicate to its own row.  The box and the cut are
+// conservative (no neighbour of a row lies outside them), so each member
+// accepts exactly its neighbours on the level, in the order (level, z, y, x,
+// sorted index) of a row-by-row walk: the lists equal the ones a per-row
+// search produces.
+
+#include <climits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -42,152 +62,266 @@ __device__ __forceinline__ float cell_gap(float x, int c, float csz, float x0, f
     return fmaxf(0.0f, fmaxf(below, above) - m);
 }
 
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNbWarps = 4;   // warps (row groups of 32) per block
+// rows whose cell lies within this many cells of the leader's join its group
+// (2, 3 and 4 measured; 3 and 4 within 1% of each other, 2 is 10% slower)
+constexpr int kNbGroupReach = 3;
+
 // MODE: NB_COUNT counts own entries (and reverse entries of the coarser
 // partners); NB_FILL writes own and reverse entries into their CSR places;
 // NB_STAGE counts like NB_COUNT and also writes the first stage_k own
-// entries of the row to stage[i * stage_k + c] (rows with more are queued on
-// the overflow list); NB_FILL_LISTED runs NB_FILL for the queued rows only.
+// entries of the row to stage[i * stage_k + c], coarser partners with the top
+// bit set (rows with more are queued on the overflow list); NB_FILL_LISTED
+// runs NB_FILL for the queued rows only.
 enum { NB_COUNT = 0, NB_FILL = 1, NB_STAGE = 2, NB_FILL_LISTED = 3 };
 
+// Append j to the own part of row i, and count or place the reverse entry
+// (i in the row of j) when j sits on a coarser level.
 template <int MODE>
-__global__ void __launch_bounds__(128, 8) nb_kernel(NbArgs a) {
+__device__ __forceinline__ void nb_accept(const NbArgs &a, int i, int j, bool coarser,
+                                          long long base, int &cnt) {
     constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (MODE == NB_FILL_LISTED) {
-        if (i >= *a.list_count) return;
-        i = a.list[i];
+    if (FILL) {
+        const long long w = base + cnt;
+        if (w < a.capacity) a.nb_idx[w] = j;
+        else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+        if (coarser) {
+            const int pos = atomicAdd(&a.rev[j], 1);
+            const long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
+            if (wr < a.capacity) a.nb_idx[wr] = i;
+            else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+        }
+    } else {
+        // the top bit marks a coarser partner for the copy pass
+        if (MODE == NB_STAGE && cnt < a.stage_k)
+            a.stage[(long long)i * a.stage_k + cnt] = coarser ? (int)((unsigned)j | 0x80000000u) : j;
+        if (coarser) atomicAdd(&a.rev[j], 1);
     }
-    if (i >= a.n) return;
+    ++cnt;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
+    constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
+    __shared__ float4 s_q[kNbWarps][32];
+    __shared__ int s_j[kNbWarps][32];
+    const int lane = threadIdx.x & 31;
+    float4 *sq = s_q[threadIdx.x >> 5];
+    int *sj = s_j[threadIdx.x >> 5];
+    const long long r = ((long long)blockIdx.x * kNbWarps + (threadIdx.x >> 5)) * 32 + lane;
+    const int rows = MODE == NB_FILL_LISTED ? *a.list_count : a.n;
+    const bool act = r < rows;
+    unsigned todo = __ballot_sync(kFull, act);
+    if (todo == 0u) return;   // the whole warp lies past the last row
+    const int i = act ? (MODE == NB_FILL_LISTED ? a.list[r] : (int)r) : 0;
     const GridDev g = *a.grid;
-    const float4 p = a.pos_h_s[i];
+    const float4 p = act ? a.pos_h_s[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int li = level_of(p.w, g.log2_L0, g.n_levels);
-    const int si = a.sim_s ? a.sim_s[i] : 0;
+    const int si = (act && a.sim_s) ? a.sim_s[i] : 0;
     int cnt = 0;
     long long base = 0;
-    if (FILL) base = a.nb_start[i];
-    for (int l = li; l < g.n_levels; ++l) {
-        if (a.lvl_count[l] == 0) continue;
-        const float R = __fadd_rn(p.w, __uint_as_float(a.lvl_hmax[l]));
-        if (!(R >= 0.0f)) continue;
-        const float inv_c = pow2f(-g.log2_L0 - l);
-        int lx, hx, ly, hy, lz, hz;
-        search_box(p.x, R, g.x0, inv_c, lx, hx);
-        search_box(p.y, R, g.y0, inv_c, ly, hy);
-        search_box(p.z, R, g.z0, inv_c, lz, hz);
-        long long ncell = (long long)(hx - lx + 1) * (hy - ly + 1) * (hz - lz + 1);
-        if (ncell > (1ll << 24)) {
-            set_flag(a.flags, SPH_FLAG_SEARCH_WIDE);
-            continue;
+    if (FILL && act) base = a.nb_start[i];
+    while (todo) {
+        // the next group: the lowest pending row and the pending rows of its
+        // simulation and level whose cells are near the leader's
+        const int ld = __ffs(todo) - 1;
+        const int lg = __shfl_sync(kFull, li, ld);
+        const int sg = __shfl_sync(kFull, si, ld);
+        bool mem;
+        {
+            const float inv_g = pow2f(-g.log2_L0 - lg);
+            const int cx = cell_of(p.x, g.x0, inv_g), cy = cell_of(p.y, g.y0, inv_g),
+                      cz = cell_of(p.z, g.z0, inv_g);
+            const int gx = __shfl_sync(kFull, cx, ld), gy = __shfl_sync(kFull, cy, ld),
+                      gz = __shfl_sync(kFull, cz, ld);
+            mem = ((todo >> lane) & 1u) && li == lg && si == sg && abs(cx - gx) <= kNbGroupReach &&
+                  abs(cy - gy) <= kNbGroupReach && abs(cz - gz) <= kNbGroupReach;
         }
-        if (a.occ && l > li) {
-            // skip the level when none of the super-cells the box touches holds
-            // a particle of it (the particle's own level is always occupied)
-            bool any = false;
-            for (int sz = lz >> kSuperShift; sz <= (hz >> kSuperShift) && !any; ++sz)
-                for (int sy = ly >> kSuperShift; sy <= (hy >> kSuperShift) && !any; ++sy)
-                    for (int sx = lx >> kSuperShift; sx <= (hx >> kSuperShift) && !any; ++sx) {
-                        const unsigned bit = super_bit(sx, sy, sz, l + kMaxLevels * si, a.log2_B);
-                        any = (a.occ[bit >> 5] >> (bit & 31)) & 1u;
-                    }
-            if (!any) continue;
-        }
-        // per-axis distance from the particle to each probed cell, widened by a
-        // margin that covers the rounding of the binning (a skipped cell cannot
-        // hold a particle within h_i + hmax of the cell's bucket)
-        const float csz = pow2f(g.log2_L0 + l);
-        // |coordinate| of anything in the box is at most |x0| + (hi + 1) csz
-        const float mx = 9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f;
-        const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
-        const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
-        // bucket_of(cx, cy, cz, ...) with the interleave built per axis: z
-        // once per plane, y once per row, x stepped by a dilated increment
-        const unsigned salt = (unsigned)(l + kMaxLevels * si) * (unsigned)kLevelSalt;
-        const unsigned kmask = (1u << g.log2_M) - 1u;
-        const unsigned dlx = spread3_lo((unsigned)lx);
-        for (int cz = lz; cz <= hz; ++cz) {
-            const float dz = cell_gap(p.z, cz, csz, g.z0, mz);
-            const unsigned iz = spread3_lo((unsigned)cz) << 2;
-            for (int cy = ly; cy <= hy; ++cy) {
-                const float dy = cell_gap(p.y, cy, csz, g.y0, my);
-                const unsigned iyz = iz | (spread3_lo((unsigned)cy) << 1);
-                unsigned ix = dlx;
-                for (int cx = lx; cx <= hx; ++cx, ix = spread3_next(ix)) {
-                    const float dx = cell_gap(p.x, cx, csz, g.x0, mx);
-                    const int k = (int)(((ix | iyz) + salt) & kmask);
-                    const int s = a.cell_start[k], e = a.cell_start[k + 1];
-                    if (s == e) continue;
-                    {
-                        const float reach = p.w + __uint_as_float(a.hmax_cell[k]);
-                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (d2 > reach * reach * (1.0f + 3.0517578125e-05f)) continue;
-                    }
-                    // candidates four at a time: their loads are issued together
-                    for (int j0 = s; j0 < e; j0 += 4) {
-                    float4 qb[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        qb[u] = j0 + u < e ? a.pos_h_s[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = j0 + u;
-                        if (j >= e || j == i) continue;
-                        const float4 q = qb[u];
-                        // the distance test first: most candidates fail it, and
-                        // the identity checks (same simulation, level and cell
-                        // as the probed one) are only needed for those that pass
-                        if (!nb_pred(p, q)) continue;
-                        if (a.sim_s && a.sim_s[j] != si) continue;
-                        if (level_of(q.w, g.log2_L0, g.n_levels) != l) continue;
-                        if (cell_of(q.x, g.x0, inv_c) != cx || cell_of(q.y, g.y0, inv_c) != cy ||
-                            cell_of(q.z, g.z0, inv_c) != cz)
-                            continue;
-                        if (FILL) {
-                            long long w = base + cnt;
-                            if (w < a.capacity) a.nb_idx[w] = j;
-                            else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
-                            if (l > li) {
-                                int pos = atomicAdd(&a.rev[j], 1);
-                                long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
-                                if (wr < a.capacity) a.nb_idx[wr] = i;
-                                else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+        todo &= ~__ballot_sync(kFull, mem);
+        const unsigned salt_sim = (unsigned)(kMaxLevels * sg);
+        for (int l = lg; l < g.n_levels; ++l) {
+            if (a.lvl_count[l] == 0) continue;
+            const float R = __fadd_rn(p.w, __uint_as_float(a.lvl_hmax[l]));
+            const float inv_c = pow2f(-g.log2_L0 - l);
+            int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
+            bool on = mem && R >= 0.0f;
+            if (on) {
+                search_box(p.x, R, g.x0, inv_c, lx, hx);
+                search_box(p.y, R, g.y0, inv_c, ly, hy);
+                search_box(p.z, R, g.z0, inv_c, lz, hz);
+                const long long ncell = (long long)(hx - lx + 1) * (hy - ly + 1) * (hz - lz + 1);
+                if (ncell > (1ll << 24)) {
+                    set_flag(a.flags, SPH_FLAG_SEARCH_WIDE);
+                    on = false;
+                }
+            }
+            unsigned pend = __ballot_sync(kFull, on);
+            if (pend == 0u) continue;
+            // a union box above the one-row cap is walked row by row (only
+            // top-level rows, whose h may exceed the level's cells, get here)
+            bool solo;
+            {
+                const int ux = __reduce_max_sync(kFull, on ? hx : INT_MIN) -
+                               __reduce_min_sync(kFull, on ? lx : INT_MAX);
+                const int uy = __reduce_max_sync(kFull, on ? hy : INT_MIN) -
+                               __reduce_min_sync(kFull, on ? ly : INT_MAX);
+                const int uz = __reduce_max_sync(kFull, on ? hz : INT_MIN) -
+                               __reduce_min_sync(kFull, on ? lz : INT_MAX);
+                solo = (long long)(ux + 1) * (uy + 1) * (uz + 1) > (1ll << 24);
+            }
+            const float csz = pow2f(g.log2_L0 + l);
+            // |coordinate| of anything in the row's box is at most |x0| + (hi + 1) csz
+            const float mx = 9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f;
+            const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
+            const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
+            const unsigned salt = ((unsigned)l + salt_sim) * (unsigned)kLevelSalt;
+            const unsigned kmask = (1u << g.log2_M) - 1u;
+            while (pend) {
+                const unsigned part = solo ? (pend & (0u - pend)) : pend;
+                pend &= ~part;
+                const bool in = (part >> lane) & 1u;
+                const int LX = __reduce_min_sync(kFull, in ? lx : INT_MAX);
+                const int HX = __reduce_max_sync(kFull, in ? hx : INT_MIN);
+                const int LY = __reduce_min_sync(kFull, in ? ly : INT_MAX);
+                const int HY = __reduce_max_sync(kFull, in ? hy : INT_MIN);
+                const int LZ = __reduce_min_sync(kFull, in ? lz : INT_MAX);
+                const int HZ = __reduce_max_sync(kFull, in ? hz : INT_MIN);
+                if (a.occ && l > lg) {
+                    // skip the level when none of the super-cells the box
+                    // touches holds a particle of it (the rows' own level is
+                    // always occupied)
+                    bool any = false;
+                    for (int sz = LZ >> kSuperShift; sz <= (HZ >> kSuperShift) && !any; ++sz)
+                        for (int sy = LY >> kSuperShift; sy <= (HY >> kSuperShift) && !any; ++sy)
+                            for (int sx = LX >> kSuperShift; sx <= (HX >> kSuperShift) && !any; ++sx) {
+                                const unsigned bit = super_bit(sx, sy, sz, l + kMaxLevels * sg, a.log2_B);
+                                any = (a.occ[bit >> 5] >> (bit & 31)) & 1u;
                             }
-                        } else {
-                            if (MODE == NB_STAGE && cnt < a.stage_k)
-                                a.stage[(long long)i * a.stage_k + cnt] = j;
-                            if (l > li) atomicAdd(&a.rev[j], 1);
-                        }
-                        ++cnt;
+                    if (!any) continue;
+                }
+                // The union box is walked 32 cells at a time in z, y, x order:
+                // lane t probes cell c0 + t, so the bucket reads of 32 cells
+                // are one round trip.  A row's predicate sees only its own
+                // level's candidates (its h is replaced by NaN, which fails
+                // every test, when it takes no part in this level).
+                const float4 pr = make_float4(p.x, p.y, p.z, in ? p.w : __uint_as_float(0x7fc00000u));
+                const int NX = HX - LX + 1, NY = HY - LY + 1;
+                const int ncell = NX * NY * (HZ - LZ + 1);
+                for (int c0 = 0; c0 < ncell; c0 += 32) {
+                    const int ct = c0 + lane;
+                    const int qx = ct / NX, ty = qx / NY;
+                    const int tx = LX + (ct - qx * NX), tyy = LY + (qx - ty * NY), tz = LZ + ty;
+                    int s = 0, e = 0;
+                    unsigned hm = 0u;
+                    if (ct < ncell) {
+                        const unsigned m = spread3_lo((unsigned)tx) | (spread3_lo((unsigned)tyy) << 1) |
+                                           (spread3_lo((unsigned)tz) << 2);
+                        const int k = (int)((m + salt) & kmask);
+                        s = a.cell_start[k];
+                        e = a.cell_start[k + 1];
+                        hm = a.hmax_cell[k];
                     }
+                    unsigned live = __ballot_sync(kFull, s < e);
+                    if (live == 0u) continue;
+                    // keep the cells some row of the group can reach: within
+                    // h_i + hmax of the bucket, widened by the binning's
+                    // rounding margin (a conservative cut, as the box is)
+                    unsigned want = 0u;
+                    for (unsigned lv = live; lv; lv &= lv - 1u) {
+                        const int t = __ffs(lv) - 1;
+                        const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
+                                  cz = __shfl_sync(kFull, tz, t);
+                        const float reach = p.w + __uint_as_float(__shfl_sync(kFull, hm, t));
+                        const float dx = cell_gap(p.x, cx, csz, g.x0, mx);
+                        const float dy = cell_gap(p.y, cy, csz, g.y0, my);
+                        const float dz = cell_gap(p.z, cz, csz, g.z0, mz);
+                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const bool need = in && !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
+                        if (__ballot_sync(kFull, need)) want |= 1u << t;
+                    }
+                    // the candidates of the kept cells, numbered in cell order
+                    const int len = ((want >> lane) & 1u) ? e - s : 0;
+                    int incl = len;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int total = __shfl_sync(kFull, incl, 31);
+                    for (int b0 = 0; b0 < total; b0 += 32) {
+                        // candidate b0 + lane: its cell t is the number of
+                        // cells whose running end does not pass it
+                        const int gi = b0 + lane;
+                        int t = 0;
+#pragma unroll
+                        for (int st = 16; st >= 1; st >>= 1)
+                            if (__shfl_sync(kFull, incl, t + st - 1) <= gi) t += st;
+                        t = min(t, 31);
+                        const int jl = __shfl_sync(kFull, s, t) + gi -
+                                       (__shfl_sync(kFull, incl, t) - __shfl_sync(kFull, len, t));
+                        const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
+                                  cz = __shfl_sync(kFull, tz, t);
+                        bool ok = gi < total && (unsigned)jl < (unsigned)a.n;
+                        float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (ok) {
+                            // the identity checks (same simulation, level and
+                            // cell as the probed one), once per candidate
+                            q = a.pos_h_s[jl];
+                            ok = (!a.sim_s || a.sim_s[jl] == sg) &&
+                                 level_of(q.w, g.log2_L0, g.n_levels) == l &&
+                                 cell_of(q.x, g.x0, inv_c) == cx && cell_of(q.y, g.y0, inv_c) == cy &&
+                                 cell_of(q.z, g.z0, inv_c) == cz;
+                        }
+                        const unsigned okm = __ballot_sync(kFull, ok);
+                        const int nok = __popc(okm);
+                        __syncwarp();   // the previous batch has been read
+                        if (ok) {
+                            const int slot = __popc(okm & ((1u << lane) - 1u));
+                            sq[slot] = q;
+                            sj[slot] = jl;
+                        }
+                        __syncwarp();
+                        for (int u = 0; u < nok; ++u) {
+                            const float4 qt = sq[u];
+                            const int jt = sj[u];
+                            if (nb_pred(pr, qt) && jt != i) nb_accept<MODE>(a, i, jt, l > lg, base, cnt);
+                        }
                     }
                 }
             }
         }
     }
-    if (!FILL) a.own[i] = cnt;
-    if (MODE == NB_STAGE && cnt > a.stage_k) a.list[atomicAdd(a.list_count, 1)] = i;
+    if (act) {
+        if (!FILL) a.own[i] = cnt;
+        if (MODE == NB_STAGE && cnt > a.stage_k) a.list[atomicAdd(a.list_count, 1)] = i;
+    }
 }
 
 // Second half of the single-search build: copy each staged row into its CSR
 // place and append the row to the reverse part of every coarser partner
-// (rows on the overflow list are filled by NB_FILL_LISTED instead).
-__global__ void __launch_bounds__(128) nb_copy_kernel(NbArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// (rows on the overflow list are filled by NB_FILL_LISTED instead).  One warp
+// per row, lanes over its entries, so reads and writes are coalesced; the
+// search marked the coarser partners with the top bit of the staged index.
+constexpr int kCopyWarps = 8;
+__global__ void __launch_bounds__(kCopyWarps * 32) nb_copy_kernel(NbArgs a) {
+    const long long i = ((long long)blockIdx.x * kCopyWarps + (threadIdx.x >> 5));
+    const int lane = threadIdx.x & 31;
     if (i >= a.n) return;
     const int cnt = a.own[i];
     if (cnt > a.stage_k) return;
-    const GridDev g = *a.grid;
-    const int li = level_of(a.pos_h_s[i].w, g.log2_L0, g.n_levels);
     const long long base = a.nb_start[i];
-    const int *row = a.stage + (long long)i * a.stage_k;
-    for (int c = 0; c < cnt; ++c) {
-        const int j = row[c];
+    const int *row = a.stage + i * a.stage_k;
+    for (int c = lane; c < cnt; c += 32) {
+        const int v = row[c];
+        const int j = v & 0x7fffffff;
         const long long w = base + c;
         if (w < a.capacity) a.nb_idx[w] = j;
         else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
-        if (level_of(a.pos_h_s[j].w, g.log2_L0, g.n_levels) > li) {
+        if (v < 0) {
             const int pos = atomicAdd(&a.rev[j], 1);
             const long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
-            if (wr < a.capacity) a.nb_idx[wr] = i;
+            if (wr < a.capacity) a.nb_idx[wr] = (int)i;
             else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
         }
     }
@@ -212,7 +346,7 @@ int launch_nb_count(const NbArgs &a, cudaStream_t st) {
 int launch_nb_fill(const NbArgs &a, cudaStream_t st) {
     if (a.n > 0) {
         if (a.stage) {
-            nb_copy_kernel<<<(a.n + 127) / 128, 128, 0, st>>>(a);
+            nb_copy_kernel<<<(a.n + kCopyWarps - 1) / kCopyWarps, kCopyWarps * 32, 0, st>>>(a);
             nb_kernel<NB_FILL_LISTED><<<(a.n + 127) / 128, 128, 0, st>>>(a);
             note_launch(2);
         } else {
