@@ -289,18 +289,19 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
     // SP1
     const int *sim_of = ctx->batch ? ctx->batch->d_sim_of_gas : nullptr;
     if (sim_of && n_gas != ctx->batch->n_gas) return SPH_ERR_INVALID_ARG;
-    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->occ, ctx->log2_M + 1, ctx->key,
-                         ctx->count, ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
-        return rc;
+    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->key, ctx->count, st))) return rc;
     // SP2 + SP3
     if ((rc = launch_scan_exclusive(ctx->count, M, ctx->start, ctx->block_sums, st))) return rc;
     // SP4 + canonical order inside buckets
-    if ((rc = launch_scatter(ctx->key, n_gas, ctx->start, ctx->count, ctx->perm, st))) return rc;
-    if ((rc = launch_segsort_buckets(ctx->start, M, ctx->perm, ctx->tmp, ctx->long_list,
-                                     ctx->long_count, st)))
+    if ((rc = launch_scatter(ctx->key, n_gas, ctx->start, ctx->count, ctx->tmp, st))) return rc;
+    if ((rc = launch_sort_buckets(ctx->key, n_gas, ctx->start, ctx->tmp, ctx->perm, ctx->long_list,
+                                  ctx->long_count, st)))
         return rc;
-    if ((rc = launch_gather_float4(pos, ctx->perm, n_gas, ctx->pos_h_s, st))) return rc;
-    if (sim_of && (rc = launch_gather_int(sim_of, ctx->perm, n_gas, ctx->sim_s, st))) return rc;
+    // sorted copies and the bucket / super-cell / level statistics
+    if ((rc = launch_gather_bin(pos, sim_of, ctx->perm, n_gas, ctx->grid, ctx->pos_h_s,
+                                sim_of ? ctx->sim_s : nullptr, ctx->occ, ctx->log2_M + 1,
+                                ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
+        return rc;
     ctx->sorted_batched = sim_of != nullptr;
     ctx->n_sorted = n_gas;
     ctx->nb_built = 0;

@@ -8,19 +8,23 @@ namespace sphgb {
 // sort.cu
 int launch_scan_exclusive(const int *in, int n, int *out, int *block_sums, cudaStream_t st);
 int scan_block_count(long long n);
-int launch_segsort_buckets(const int *start, int M, int *data, int *tmp, int *long_list,
-                           int *long_count, cudaStream_t st);
+// canonical order inside the buckets: unordered is the scatter's output
+// (left scrambled), perm receives each bucket's members in ascending order
+int launch_sort_buckets(const int *key, int n, const int *start, int *unordered, int *perm,
+                        int *long_list, int *long_count, cudaStream_t st);
 int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int *data, int *tmp,
                         int *long_list, int *long_count, cudaStream_t st);
 int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
                      cudaStream_t st);
 int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st);
-int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, unsigned *occ,
-               int log2_B, int *key, int *count, unsigned *hmax_cell, int *lvl_count,
-               unsigned *lvl_hmax, cudaStream_t st);
-int launch_gather_int(const int *src, const int *perm, int n, int *dst, cudaStream_t st);
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
+               int *count, cudaStream_t st);
+// sorted copies (pos_h_s, and sim_s when sim_of is given) and the bucket,
+// super-cell and level statistics, taken over the sorted order
+int launch_gather_bin(const float4 *pos_h, const int *sim_of, const int *perm, int n,
+                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *occ, int log2_B,
+                      unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st);
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
-int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st);
 void grid_reset_red(unsigned *red, const unsigned *v, cudaStream_t st);
 
 // gravity.cu: the batched kernel's work description (host side)

@@ -23,8 +23,8 @@
 namespace sphgb {
 
 // Scratch layout, each part 256-byte aligned (limits in include/sphgb.h):
-//   count[M], hmax_cell[M], long_list[max(n, M)], tmp[n], block_sums[..],
-//   lvl_count[32], lvl_hmax[32], grid, red[8], long_count[4]
+//   count[M], long_list[max(n, M)], tmp[n], block_sums[..], grid, red[8],
+//   long_count[4]
 constexpr long long kNaM = 1ll << SPH_NOALLOC_MAX_LOG2_M;
 constexpr long long kNaN = SPH_NOALLOC_MAX_GAS;
 constexpr long long kNaSeg = kNaM > kNaN ? kNaM : kNaN;
@@ -32,13 +32,10 @@ constexpr long long kNaBlocks = (kNaSeg + 1 + 4095) / 4096 + 32;
 
 constexpr size_t na_up(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCount = 0;
-constexpr size_t kOffHmax = kOffCount + na_up(sizeof(int) * kNaM);
-constexpr size_t kOffLong = kOffHmax + na_up(sizeof(unsigned) * kNaM);
+constexpr size_t kOffLong = kOffCount + na_up(sizeof(int) * kNaM);
 constexpr size_t kOffTmp = kOffLong + na_up(sizeof(int) * kNaSeg);
 constexpr size_t kOffBlocks = kOffTmp + na_up(sizeof(int) * kNaN);
-constexpr size_t kOffLvlCount = kOffBlocks + na_up(sizeof(int) * kNaBlocks);
-constexpr size_t kOffLvlHmax = kOffLvlCount + na_up(sizeof(int) * kMaxLevels);
-constexpr size_t kOffGrid = kOffLvlHmax + na_up(sizeof(unsigned) * kMaxLevels);
+constexpr size_t kOffGrid = kOffBlocks + na_up(sizeof(int) * kNaBlocks);
 constexpr size_t kOffRed = kOffGrid + na_up(sizeof(GridDev));
 constexpr size_t kOffLongCount = kOffRed + na_up(sizeof(unsigned) * 8);
 constexpr size_t kNaBytes = kOffLongCount + na_up(sizeof(int) * 4);
@@ -87,12 +84,9 @@ extern "C" int sph_bin_and_sort_noalloc(const float *d_pos_h, int32_t n_gas, int
     int rc = noalloc_scratch(&base);
     if (rc) return rc;
     int *count = reinterpret_cast<int *>(base + kOffCount);
-    unsigned *hmax = reinterpret_cast<unsigned *>(base + kOffHmax);
     int *long_list = reinterpret_cast<int *>(base + kOffLong);
     int *tmp = reinterpret_cast<int *>(base + kOffTmp);
     int *block_sums = reinterpret_cast<int *>(base + kOffBlocks);
-    int *lvl_count = reinterpret_cast<int *>(base + kOffLvlCount);
-    unsigned *lvl_hmax = reinterpret_cast<unsigned *>(base + kOffLvlHmax);
     GridDev *grid = reinterpret_cast<GridDev *>(base + kOffGrid);
     unsigned *red = reinterpret_cast<unsigned *>(base + kOffRed);
     int *long_count = reinterpret_cast<int *>(base + kOffLongCount);
@@ -105,11 +99,8 @@ extern "C" int sph_bin_and_sort_noalloc(const float *d_pos_h, int32_t n_gas, int
     if (rc) return rc;
     // the shared array keeps the previous call's contents: clear the counters
     SPH_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)M, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(hmax, 0, sizeof(unsigned) * (size_t)M, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(lvl_count, 0, sizeof(int) * kMaxLevels, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
-    if ((rc = launch_bin(pos, nullptr, n_gas, grid, nullptr, 0, d_key, count, hmax, lvl_count, lvl_hmax, st))) return rc;
+    if ((rc = launch_bin(pos, nullptr, n_gas, grid, d_key, count, st))) return rc;
     if ((rc = launch_scan_exclusive(count, M, d_cell_start, block_sums, st))) return rc;
-    if ((rc = launch_scatter(d_key, n_gas, d_cell_start, count, d_perm, st))) return rc;
-    return launch_segsort_buckets(d_cell_start, M, d_perm, tmp, long_list, long_count, st);
+    if ((rc = launch_scatter(d_key, n_gas, d_cell_start, count, tmp, st))) return rc;
+    return launch_sort_buckets(d_key, n_gas, d_cell_start, tmp, d_perm, long_list, long_count, st);
 }

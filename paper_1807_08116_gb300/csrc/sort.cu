@@ -99,15 +99,47 @@ __global__ void grid_set_kernel(GridDev g, GridDev *grid) {
 }
 
 // ---------------------------------------------------------------------------
-// SP1: bucket of each particle, bucket counts, per-bucket max h, per-level
-// count and max h.
+// SP1: bucket of each particle and the bucket counts.  The statistics the
+// neighbour search needs (per-bucket and per-level max h, per-level counts,
+// super-cell occupancy) are taken after the sort, in gather_bin_kernel, where
+// the particles of a bucket are adjacent and a warp needs one atomic per run
+// of equal values instead of one per particle on scattered addresses.
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ int bucket_of_particle(const float4 &p, int sim, const GridDev &g, int &l,
+                                                  int &cx, int &cy, int &cz) {
+    l = level_of(p.w, g.log2_L0, g.n_levels);
+    const float inv_c = pow2f(-g.log2_L0 - l);
+    cx = cell_of(p.x, g.x0, inv_c);
+    cy = cell_of(p.y, g.y0, inv_c);
+    cz = cell_of(p.z, g.z0, inv_c);
+    // simulations of a batch share the grid; the simulation index enters the
+    // bucket hash next to the level (0 for a single simulation)
+    return bucket_of(cx, cy, cz, l + kMaxLevels * sim, g.log2_M);
+}
+
 __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restrict__ sim_of, int n,
-                           const GridDev *__restrict__ gridp, unsigned *__restrict__ occ, int log2_B,
-                           int *__restrict__ key, int *__restrict__ count,
-                           unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
-                           unsigned *__restrict__ lvl_hmax) {
+                           const GridDev *__restrict__ gridp, int *__restrict__ key,
+                           int *__restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const GridDev g = *gridp;
+    int l, cx, cy, cz;
+    const int k = bucket_of_particle(pos_h[i], sim_of ? sim_of[i] : 0, g, l, cx, cy, cz);
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+}
+
+// Sorted copies of (x, y, z, h) and of the simulation index, plus the
+// statistics: hmax_cell[k] (max h of bucket k; NaN or h <= 0 count as 0),
+// the occupancy bit of every occupied super-cell (occ may be NULL), and the
+// count and max h of every level.
+__global__ void gather_bin_kernel(const float4 *__restrict__ pos_h, const int *__restrict__ sim_of,
+                                  const int *__restrict__ perm, int n,
+                                  const GridDev *__restrict__ gridp, float4 *__restrict__ pos_h_s,
+                                  int *__restrict__ sim_s, unsigned *__restrict__ occ, int log2_B,
+                                  unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
+                                  unsigned *__restrict__ lvl_hmax) {
     __shared__ int s_cnt[kMaxLevels];
     __shared__ unsigned s_hmax[kMaxLevels];
     if (threadIdx.x < kMaxLevels) {
@@ -116,40 +148,36 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restri
     }
     __syncthreads();
     const GridDev g = *gridp;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int l = -1;                 // level of this thread's particle (-1: none)
-    unsigned hb = 0u;
-    if (i < n) {
-        float4 p = pos_h[i];
-        l = level_of(p.w, g.log2_L0, g.n_levels);
-        float inv_c = pow2f(-g.log2_L0 - l);
-        int cx = cell_of(p.x, g.x0, inv_c);
-        int cy = cell_of(p.y, g.y0, inv_c);
-        int cz = cell_of(p.z, g.z0, inv_c);
-        // simulations of a batch share the grid; the simulation index enters
-        // the bucket hash next to the level (0 for a single simulation)
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int l = -1, k = -1;
+    unsigned hb = 0u, sbit = 0xffffffffu;   // no super-cell bit reaches 2^31
+    if (j < n) {
+        const int i = perm[j];
+        const float4 p = pos_h[i];
+        pos_h_s[j] = p;
         const int sim = sim_of ? sim_of[i] : 0;
-        int k = bucket_of(cx, cy, cz, l + kMaxLevels * sim, g.log2_M);
-        key[i] = k;
+        if (sim_s) sim_s[j] = sim;
+        int cx, cy, cz;
+        k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
         hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
-        // The occupancy word and the bucket's h maximum are shared by every
-        // particle of a dense super-cell / bucket: read before the atomic so
-        // that only the particles that change them contend (both only grow
-        // within a launch, so a stale read costs one redundant atomic).
-        if (occ) {
-            const unsigned b = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
-                                         l + kMaxLevels * sim, log2_B);
-            const unsigned bit = 1u << (b & 31);
-            if (!(__ldcg(&occ[b >> 5]) & bit)) atomicOr(&occ[b >> 5], bit);
-        }
-        atomicAdd(&count[k], 1);
-        if (__ldcg(&hmax_cell[k]) < hb) atomicMax(&hmax_cell[k], hb);
+        if (occ)
+            sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
+                             l + kMaxLevels * sim, log2_B);
     }
-    // per-level totals: one shared atomic per (warp, level) instead of one
-    // per particle
+    {
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        const unsigned m = __reduce_max_sync(peers, hb);
+        if (k >= 0 && lane == __ffs(peers) - 1 && m > 0u) atomicMax(&hmax_cell[k], m);
+    }
+    if (occ) {
+        const unsigned peers = __match_any_sync(0xffffffffu, sbit);
+        if (k >= 0 && lane == __ffs(peers) - 1) atomicOr(&occ[sbit >> 5], 1u << (sbit & 31));
+    }
+    // per-level totals: one shared atomic per (warp, level)
     const unsigned peers = __match_any_sync(0xffffffffu, l);
     const unsigned hpeer = __reduce_max_sync(peers, hb);
-    if (l >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+    if (l >= 0 && lane == __ffs(peers) - 1) {
         atomicAdd(&s_cnt[l], __popc(peers));
         atomicMax(&s_hmax[l], hpeer);
     }
@@ -250,8 +278,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_down_kernel(const int *__re
 }
 
 // ---------------------------------------------------------------------------
-// SP4: scatter with an atomic cursor (count is driven back to zero), then a
-// per-bucket sort that makes the order inside every bucket ascending.
+// SP4: scatter with an atomic cursor (count is driven back to zero), then the
+// canonical (ascending) order inside every bucket: a particle's place is the
+// number of members of its bucket with a smaller index; buckets too long for
+// that count are sorted one block per bucket.
 // ---------------------------------------------------------------------------
 
 __global__ void scatter_kernel(const int *__restrict__ key, int n, const int *__restrict__ start,
@@ -261,6 +291,28 @@ __global__ void scatter_kernel(const int *__restrict__ key, int n, const int *__
     int k = key[i];
     int pos = atomicSub(&count[k], 1) - 1;
     perm[start[k] + pos] = i;
+}
+
+constexpr int RANK_MAX = 64;
+
+// unordered: the scatter's output, each bucket's members in arbitrary order.
+// Writes perm[start[k] + rank] = i for buckets of up to RANK_MAX members and
+// queues the longer ones (once, by the member found first) for the
+// block-per-segment sort.
+__global__ void bucket_rank_kernel(const int *__restrict__ key, int n, const int *__restrict__ start,
+                                   const int *__restrict__ unordered, int *__restrict__ perm,
+                                   int *__restrict__ long_list, int *__restrict__ long_count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = key[i];
+    const int s = start[k], e = start[k + 1];
+    if (e - s > RANK_MAX) {
+        if (unordered[s] == i) long_list[atomicAdd(long_count, 1)] = k;
+        return;
+    }
+    int r = 0;
+    for (int q = s; q < e; ++q) r += unordered[q] < i;
+    perm[s + r] = i;
 }
 
 constexpr int SEG_SMALL = 32;
@@ -344,8 +396,10 @@ __device__ __forceinline__ int co_rank(int k, const int *A, int na, const int *B
     return lo;
 }
 
+// The sorted segment is left in out, which may be data itself or the
+// scratch array tmp (the three may alias, hence no __restrict__).
 template <class Seg>
-__global__ void segsort_long_kernel(Seg seg, int *__restrict__ data, int *__restrict__ tmp,
+__global__ void segsort_long_kernel(Seg seg, int *data, int *tmp, int *out,
                                     const int *__restrict__ long_list,
                                     const int *__restrict__ long_count) {
     __shared__ int sm[SEG_CHUNK];
@@ -356,6 +410,10 @@ __global__ void segsort_long_kernel(Seg seg, int *__restrict__ data, int *__rest
         const int len = e - b;
         if (len <= SEG_CHUNK) {
             chunk_sort(data, b, len, sm);
+            if (out != data) {
+                for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = data[b + q];
+                __syncthreads();
+            }
             continue;
         }
         for (int c0 = 0; c0 < len; c0 += SEG_CHUNK) chunk_sort(data, b + c0, min(SEG_CHUNK, len - c0), sm);
@@ -380,8 +438,8 @@ __global__ void segsort_long_kernel(Seg seg, int *__restrict__ data, int *__rest
             src = dst;
             dst = t;
         }
-        if (src != data) {
-            for (int q = threadIdx.x; q < len; q += blockDim.x) data[b + q] = src[b + q];
+        if (src != out) {
+            for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = src[b + q];
         }
         __syncthreads();
     }
@@ -401,18 +459,6 @@ struct RevSeg {   // reverse part of neighbour row s, clipped to the list capaci
     __device__ int begin(int s) const { return min(nb_start[s] + own[s], end(s)); }
 };
 
-__global__ void gather_int_kernel(const int *__restrict__ src, const int *__restrict__ perm, int n,
-                                  int *__restrict__ dst) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) dst[j] = src[perm[j]];
-}
-
-__global__ void gather_float4_kernel(const float4 *__restrict__ src, const int *__restrict__ perm,
-                                     int n, float4 *__restrict__ dst) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) dst[j] = src[perm[j]];
-}
-
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -431,13 +477,16 @@ int launch_scan_exclusive(const int *in, int n, int *out, int *block_sums, cudaS
 
 int scan_block_count(long long n) { return (int)blocks_for(n + 1, SCAN_TILE); }
 
-int launch_segsort_buckets(const int *start, int M, int *data, int *tmp, int *long_list,
-                           int *long_count, cudaStream_t st) {
+int launch_sort_buckets(const int *key, int n, const int *start, int *unordered, int *perm,
+                        int *long_list, int *long_count, cudaStream_t st) {
     SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
-    BucketSeg seg{start};
-    segsort_small_kernel<<<blocks_for(M, 256), 256, 0, st>>>(seg, M, data, long_list, long_count);
-    segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, long_list, long_count);
-    note_launch(2);
+    if (n > 0) {
+        bucket_rank_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key, n, start, unordered, perm,
+                                                               long_list, long_count);
+        BucketSeg seg{start};
+        segsort_long_kernel<<<1024, 256, 0, st>>>(seg, unordered, perm, perm, long_list, long_count);
+        note_launch(2);
+    }
     SPH_LAUNCH_CHECK();
     return SPH_OK;
 }
@@ -448,7 +497,7 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
     RevSeg seg{nb_start, own, cap};
     if (n == 0) return SPH_OK;
     segsort_small_kernel<<<blocks_for(n, 256), 256, 0, st>>>(seg, n, data, long_list, long_count);
-    segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, long_list, long_count);
+    segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, data, long_list, long_count);
     note_launch(2);
     SPH_LAUNCH_CHECK();
     return SPH_OK;
@@ -475,12 +524,23 @@ int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st) {
     return SPH_OK;
 }
 
-int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, unsigned *occ,
-               int log2_B, int *key, int *count, unsigned *hmax_cell, int *lvl_count,
-               unsigned *lvl_hmax, cudaStream_t st) {
+int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
+               int *count, cudaStream_t st) {
     if (n > 0) {
-        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, n, grid, occ, log2_B, key,
-                                                       count, hmax_cell, lvl_count, lvl_hmax);
+        bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, n, grid, key, count);
+        note_launch();
+    }
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
+}
+
+int launch_gather_bin(const float4 *pos_h, const int *sim_of, const int *perm, int n,
+                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *occ, int log2_B,
+                      unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st) {
+    if (n > 0) {
+        gather_bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, perm, n, grid, pos_h_s,
+                                                              sim_s, occ, log2_B, hmax_cell,
+                                                              lvl_count, lvl_hmax);
         note_launch();
     }
     SPH_LAUNCH_CHECK();
@@ -490,24 +550,6 @@ int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *gri
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st) {
     if (n > 0) {
         scatter_kernel<<<blocks_for(n, 256), 256, 0, st>>>(key, n, start, count, perm);
-        note_launch();
-    }
-    SPH_LAUNCH_CHECK();
-    return SPH_OK;
-}
-
-int launch_gather_int(const int *src, const int *perm, int n, int *dst, cudaStream_t st) {
-    if (n > 0) {
-        gather_int_kernel<<<blocks_for(n, 256), 256, 0, st>>>(src, perm, n, dst);
-        note_launch();
-    }
-    SPH_LAUNCH_CHECK();
-    return SPH_OK;
-}
-
-int launch_gather_float4(const float4 *src, const int *perm, int n, float4 *dst, cudaStream_t st) {
-    if (n > 0) {
-        gather_float4_kernel<<<blocks_for(n, 256), 256, 0, st>>>(src, perm, n, dst);
         note_launch();
     }
     SPH_LAUNCH_CHECK();
