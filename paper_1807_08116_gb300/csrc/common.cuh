@@ -65,9 +65,6 @@ __device__ __forceinline__ unsigned spread3_lo(unsigned v) {
     return x;
 }
 
-// spread3_lo(v + 1) from spread3_lo(v) (dilated-integer increment, mod 2^10).
-__device__ __forceinline__ unsigned spread3_next(unsigned d) { return ((d | ~kDilatedX) + 1u) & kDilatedX; }
-
 // Bucket of cell (cx, cy, cz) on level tag l: (interleave + l * kLevelSalt)
 // mod 2^log2_M, log2_M <= 30.
 __device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2_M) {
@@ -77,8 +74,8 @@ __device__ __forceinline__ int bucket_of(int cx, int cy, int cz, int l, int log2
 }
 
 // Occupancy bit of a super-cell (8 x 8 x 8 cells of one level): set by the
-// binning for every occupied super-cell, read by the neighbour search to skip
-// levels with nobody near.  Hash collisions only cost a wasted probe.
+// sorting stage for every occupied super-cell, read by the neighbour search to
+// skip levels with nobody near.  Hash collisions only cost a wasted probe.
 constexpr int kSuperShift = 3;
 constexpr unsigned long long kSuperSalt = 0xD1B54A32D192ED03ull;
 __device__ __forceinline__ unsigned super_bit(int sx, int sy, int sz, int l, int log2_B) {
