@@ -282,10 +282,17 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                             sj[slot] = jl;
                         }
                         __syncwarp();
-                        for (int u = 0; u < nok; ++u) {
-                            const float4 qt = sq[u];
+                        // the predicate over the batch first, collecting a
+                        // bit per accepted candidate; then the appends, in
+                        // candidate order, with no branch per candidate
+                        unsigned acc = 0u;
+                        for (int u = 0; u < nok; ++u)
+                            if (nb_pred(pr, sq[u])) acc |= 1u << u;
+                        while (acc) {
+                            const int u = __ffs(acc) - 1;
+                            acc &= acc - 1u;
                             const int jt = sj[u];
-                            if (nb_pred(pr, qt) && jt != i) nb_accept<MODE>(a, i, jt, l > lg, base, cnt);
+                            if (jt != i) nb_accept<MODE>(a, i, jt, l > lg, base, cnt);
                         }
                     }
                 }
