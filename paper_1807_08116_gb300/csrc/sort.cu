@@ -9,9 +9,12 @@
 // atomics (O(G^2) adds), SP3 adds the block offsets, SP4 scatters with an
 // atomic cursor.  Here SP2/SP3 become a reduce-then-scan cascade (warp
 // shuffles, then shared memory, then one pass over block totals) with no
-// spin-waits, and SP4's arbitrary within-bucket order is repaired by a
-// segmented sort of each bucket.
+// spin-waits, and SP4's arbitrary within-bucket order is repaired by a rank
+// pass (a particle's place is the number of its bucket's members with a
+// smaller index).  The same file holds the segmented sort that orders the
+// reverse part of each neighbour row.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -315,33 +318,43 @@ __global__ void bucket_rank_kernel(const int *__restrict__ key, int n, const int
     perm[s + r] = i;
 }
 
-constexpr int SEG_SMALL = 32;
+constexpr int WARP_RANK_MAX = 64;
 
-// One thread per segment [begin(s), end(s)): insertion sort when short,
-// otherwise queue the segment for the block-per-segment pass.
+// One warp per segment [begin(s), end(s)) of distinct values: each value's
+// place is the number of smaller values in the segment (counted over the
+// values held in registers, up to two per lane), written back in place.
+// Longer segments are queued for the block-per-segment pass.
 template <class Seg>
-__global__ void segsort_small_kernel(Seg seg, int nseg, int *__restrict__ data,
-                                     int *__restrict__ long_list, int *__restrict__ long_count) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg) return;
-    int b = seg.begin(s), e = seg.end(s);
-    int len = e - b;
+__global__ void __launch_bounds__(256) seg_rank_kernel(Seg seg, int nseg, int *data,
+                                                       int *__restrict__ long_list,
+                                                       int *__restrict__ long_count) {
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nseg) return;   // the whole warp
+    const int s = (int)w;
+    const int b = seg.begin(s), len = seg.end(s) - b;
     if (len <= 1) return;
-    if (len > SEG_SMALL) {
-        int q = atomicAdd(long_count, 1);
-        long_list[q] = s;
+    if (len > WARP_RANK_MAX) {
+        if (lane == 0) long_list[atomicAdd(long_count, 1)] = s;
         return;
     }
-    // insertion sort in place (segments are short; the lines stay in L1)
-    for (int q = b + 1; q < e; ++q) {
-        int x = data[q];
-        int r = q - 1;
-        while (r >= b && data[r] > x) {
-            data[r + 1] = data[r];
-            --r;
-        }
-        data[r + 1] = x;
+    const int v0 = lane < len ? data[b + lane] : INT_MAX;
+    const int v1 = lane + 32 < len ? data[b + 32 + lane] : INT_MAX;
+    int r0 = 0, r1 = 0;
+    const int n0 = len < 32 ? len : 32;
+    for (int t = 0; t < n0; ++t) {
+        const int x = __shfl_sync(0xffffffffu, v0, t);
+        r0 += x < v0;
+        r1 += x < v1;
     }
+    for (int t = 32; t < len; ++t) {
+        const int x = __shfl_sync(0xffffffffu, v1, t - 32);
+        r0 += x < v0;
+        r1 += x < v1;
+    }
+    __syncwarp();
+    if (lane < len) data[b + r0] = v0;
+    if (lane + 32 < len) data[b + r1] = v1;
 }
 
 // One block per long segment.  Segments of up to SEG_CHUNK values are
@@ -496,7 +509,8 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
     SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
     RevSeg seg{nb_start, own, cap};
     if (n == 0) return SPH_OK;
-    segsort_small_kernel<<<blocks_for(n, 256), 256, 0, st>>>(seg, n, data, long_list, long_count);
+    seg_rank_kernel<<<blocks_for((long long)n * 32, 256), 256, 0, st>>>(seg, n, data, long_list,
+                                                                        long_count);
     segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, data, long_list, long_count);
     note_launch(2);
     SPH_LAUNCH_CHECK();

@@ -263,3 +263,38 @@ def test_two_pass_fallback_when_scratch_is_small(orc):
     b = _lists(big, n)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     _check_lists(orc, ph, small, perm, rows=np.arange(0, n, 7))
+
+
+def _levels_sorted(orc, ph, grid, perm):
+    level, _, _ = orc.bin_particles(ph, grid)
+    return level[perm]
+
+
+@pytest.mark.parametrize("n_wide", [40, 70, 200])
+def test_row_layout_own_then_reverse_ascending(orc, n_wide):
+    # wide particles among narrow ones get reverse parts of about 20-300
+    # entries (both sides of the 32- and 64-entry limits of the per-warp
+    # ranking); every row must hold its own-level-and-up part first and its
+    # finer-level partners after it in ascending order, and the sets must be
+    # the brute-force ones
+    rng = np.random.default_rng(31 + n_wide)
+    narrow = pos_h_of(rng.uniform(0, 1, size=(6000, 3)), np.full(6000, 0.04))
+    wide = pos_h_of(rng.uniform(0.1, 0.9, size=(n_wide, 3)), rng.uniform(0.06, 0.2, n_wide))
+    ph = np.concatenate([narrow, wide]).astype(np.float32)
+    ph = ph[rng.permutation(len(ph))]
+    n = len(ph)
+    ctx = _ctx(n)
+    grid = _auto_grid(ph, ctx.log2_M)
+    ctx, perm = _check_sort(orc, ph, grid, ctx)
+    start, idx, _ = _check_lists(orc, ph, ctx, perm)
+    lv = _levels_sorted(orc, ph, grid, perm)
+    lens = []
+    for s in range(n):
+        row = idx[start[s]:start[s + 1]]
+        finer = lv[row] < lv[s]
+        k = int(finer.sum())
+        lens.append(k)
+        assert not finer[:len(row) - k].any(), f"row {s}: a finer partner before the own part ends"
+        assert np.all(np.diff(row[len(row) - k:]) > 0), f"row {s}: reverse part not ascending"
+    lens = np.array(lens)
+    assert lens.max() > 64 and ((lens > 1) & (lens <= 32)).any() and ((lens > 32) & (lens <= 64)).any()
