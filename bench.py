@@ -281,6 +281,23 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def energy_momentum(sim):
+    """Total energy (kinetic + thermal + potential, FP64 sums) and momentum of
+    a simulation's current state; the potential comes from one extra gravity
+    evaluation with the potential flag on the FP32 positions."""
+    import torch
+
+    from paper_1807_08116_gb300 import native as nv
+    d = sim.diagnostics()
+    phi = torch.empty_like(sim.t["pos_m"])
+    nv.pp_gravity(sim.t["pos_m"], phi, G=sim.params["G"], eps=sim.params["eps"],
+                  flags=nv.SPH_GRAV_POTENTIAL)
+    pot = 0.5 * float((sim.t["mass"].double() * phi[:, 3].double()).sum())
+    p = np.asarray(d["momentum"], dtype=np.float64)
+    return {"E": float(d["kinetic"] + d["thermal"] + pot), "p": p,
+            "p_scale": float(np.sqrt(2.0 * d["kinetic"] * d["mass"]))}
+
+
 def run_ours(args):
     import torch
 
@@ -309,6 +326,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         sim.step(dt)
     torch.cuda.synchronize()
+
+    cons0 = energy_momentum(sim) if args.conservation else None
 
     # ---- device-resident timed region ------------------------------------
     evs = [nv.StageEvents() for _ in range(args.steps)]
@@ -340,6 +359,14 @@ def run_ours(args):
         e.close()
     ms = max_over_ranks(ms, dist, "cuda")
     value = aggregate_rate(world, n, args.steps, ms)
+    conservation = None
+    if cons0 is not None:
+        cons1 = energy_momentum(sim)
+        conservation = {
+            "steps": args.steps, "dt": dt, "E0": cons0["E"], "E1": cons1["E"],
+            "dE_over_E": abs(cons1["E"] - cons0["E"]) / abs(cons0["E"]),
+            "dp_over_p_scale": float(np.abs(cons1["p"] - cons0["p"]).max() / cons0["p_scale"]),
+            "note": "outside the timed region; potential from a separate gravity evaluation"}
 
     # ---- end to end through the C ABI with host buffers --------------------
     e2e = None
@@ -393,9 +420,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_NAMES[args.workload], "n": n, "n_gas": ng, "dt": dt,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state and lists > 129 MB)",
-                       "precision": "FP32 forces (Kahan), FP64 leapfrog state"},
+                       "precision": "FP32 forces (compensated sums), FP64 leapfrog state"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "stage_ms": stage,
+            "clocks": clk, "stage_ms": stage, **({"conservation": conservation} if conservation else {}),
             "stage_roofline": stage_roofline(stage, n, ng, nb_entries),
         }
         print(json.dumps(line), flush=True)
@@ -649,6 +676,8 @@ def main(argv=None):
     ap.add_argument("--serve-window", type=float, default=90.0)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--max-resident", type=int, default=16)
+    ap.add_argument("--conservation", action="store_true",
+                    help="report the energy and momentum change over the timed steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
