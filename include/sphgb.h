@@ -48,7 +48,7 @@ typedef struct CUstream_st *sph_stream_t;
 #define SPH_FLAG_NB_OVERFLOW   1   /* neighbour entries beyond capacity were dropped */
 #define SPH_FLAG_SEARCH_WIDE   2   /* a search box exceeded 2^24 cells and was skipped */
 #define SPH_FLAG_TIMEOUT       4   /* a bounded mbarrier wait gave up */
-#define SPH_FLAG_ROW_UNSORTED  8   /* a segment too long to canonicalise was left as is */
+#define SPH_FLAG_ROW_UNSORTED  8   /* reserved: never set (segments of any length are canonicalised) */
 #define SPH_FLAG_GRAV_RANGE   16   /* pp_gravity_pairs: masses / eps put its fixed-point scale out of range */
 
 /* Model constants (Sect. 2): gravitational constant G and softening length

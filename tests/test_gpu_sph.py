@@ -141,6 +141,29 @@ def test_two_halo_sampled_rows(orc):
     assert re <= RMS_TOL and me <= MAX_TOL
 
 
+def test_large_collision_sampled_rows(orc):
+    # the 2 x (1048576 + 1048576) collision, in the launch configuration of
+    # its steps (2 lanes per row, the tuned choice at this size): density on
+    # sampled rows against brute force; forces on sampled rows from a common
+    # density input (the GPU densities, which both sides then read)
+    d = ics.two_halo(1048576, 1048576, seed=2)
+    ph, mass, ve = _stirred(d, seed=3)
+    n = len(ph)
+    rows = np.random.default_rng(7).choice(n, 48, replace=False)
+    _, rho, _ = _density(ph, mass, lanes=2)
+    orho, _ = orc.density(ph, mass, rows=rows)
+    r1, m1 = err(rho[rows], orho)
+    a = _forces(ph, ve, mass, rho, lanes=2)
+    oa, ode = orc.hydro(ph, ve, mass, rho, rows=rows)
+    ra, ma = err(a[rows, :3], oa)
+    re, me = err(a[rows, 3:], ode[:, None])
+    print(f"large-collision sample: rho rms {r1:.2e} max {m1:.2e}; accel rms {ra:.2e} "
+          f"max {ma:.2e}; de/dt rms {re:.2e} max {me:.2e}")
+    assert r1 <= RHO_RMS and m1 <= RHO_MAX
+    assert ra <= RMS_TOL and ma <= MAX_TOL
+    assert re <= RMS_TOL and me <= MAX_TOL
+
+
 def test_isolated_and_empty():
     torch = need_gpu()
     from paper_1807_08116_gb300 import native as nv
