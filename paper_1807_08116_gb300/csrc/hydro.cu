@@ -2,9 +2,10 @@
 // spline of Eq. 8) and the hydrodynamic force HFC (Eqs. 10-11 with the
 // pressure kernel of Eq. 9 and Monaghan's viscosity, Sect. 2.2).
 //
-// Both run in sorted (bucket) order over the CSR neighbour lists: one thread
-// per row, FP32 arithmetic, Kahan-compensated sums, results scattered back
-// to the caller's order through perm.  The working set of a row's
+// Both run in sorted (bucket) order over the CSR neighbour lists: G lanes
+// per row, FP32 arithmetic (the pair terms use the hardware reciprocal square
+// root and the fast 2-ulp division; the sums are Kahan-compensated), results
+// scattered back to the caller's order through perm.  The working set of a row's
 // neighbours (16-48 bytes each) is read through L1/L2; the lists themselves
 // stream from HBM.
 #include <cstring>
@@ -21,6 +22,17 @@ __device__ __forceinline__ float spline_shape(float xi) {
     if (xi <= 1.0f) return fmaf(xi * xi, fmaf(0.75f, xi, -1.5f), 1.0f);
     float t = 2.0f - xi;
     return xi < 2.0f ? 0.25f * t * t * t : 0.0f;
+}
+
+// |dr| from |dr|^2 with the hardware reciprocal square root (2 ulp); 0 at 0.
+__device__ __forceinline__ float pair_dist(float r2) {
+    return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+}
+
+// mu_ij of Monaghan's viscosity (after Eq. 11), h_ij dr.dv / (|dr|^2 + eta h_ij^2),
+// with the fast division (2 ulp); the force pass and the Eq. 17 pass share it.
+__device__ __forceinline__ float visc_mu(float hij, float rv, float r2, float eta) {
+    return __fdividef(hij * rv, fmaf(eta * hij, hij, r2));
 }
 
 // Lanes of one row's group: G consecutive lanes of a warp (G divides 32).
@@ -103,10 +115,9 @@ density_kernel(const float4 *__restrict__ pos_h_s, const float *__restrict__ mas
         if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
         const float4 o = pos_h_s[j];
         const float mj = mass_s[j];
-        float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
-        float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        float hij = 0.5f * (hi + o.w);
-        float ih = 1.0f / hij;
+        const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
+        const float r = pair_dist(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float ih = __fdividef(1.0f, 0.5f * (hi + o.w));
         acc.add(mj * (ih * ih * ih) * kInvPi * spline_shape(r * ih));
     }
     const float rho = group_sum<G>(acc.s - acc.c, mask);
@@ -184,19 +195,20 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
         const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
         const float dvx = v.x - w.x, dvy = v.y - w.y, dvz = v.z - w.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float r = sqrtf(r2);
+        const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        const float r = r2 * rinv;
         const float hij = 0.5f * (p.w + o.w);
-        const float ih = 1.0f / hij;
+        const float ih = __fdividef(1.0f, hij);
         const float tt = fmaxf(2.0f - r * ih, 0.0f);
         // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
-        const float f = r > 0.0f ? kdw * (ih * ih * ih) * tt * tt * ih / r : 0.0f;
+        const float f = kdw * (ih * ih * ih) * tt * tt * ih * rinv;
         const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
         const float c_ij = 0.5f * (ai.w + aj.w);
         float nu = 0.0f;
         if (rv < 0.0f) {
-            const float mu = hij * rv / fmaf(hp.eta * hij, hij, r2);
+            const float mu = visc_mu(hij, rv, r2, hp.eta);
             const float rho_ij = 0.5f * (ai.y + aj.y);
-            nu = mu * fmaf(hp.beta, mu, -hp.alpha * c_ij) / rho_ij;
+            nu = __fdividef(mu * fmaf(hp.beta, mu, -hp.alpha * c_ij), rho_ij);
             if (CFL) mu_max = fmaxf(mu_max, -mu);
         }
         if (CFL) {
@@ -261,10 +273,8 @@ cfl_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel_s,
             s_min = fminf(s_min, sqrtf(r2));
             c_max = fmaxf(c_max, 0.5f * (ci + aux_s[j].w));
             const float rv = fmaf(dx, v.x - w.x, fmaf(dy, v.y - w.y, dz * (v.z - w.z)));
-            if (rv < 0.0f) {
-                const float hij = 0.5f * (p.w + q.w);
-                mu_max = fmaxf(mu_max, -hij * rv / fmaf(hp.eta * hij, hij, r2));
-            }
+            if (rv < 0.0f)
+                mu_max = fmaxf(mu_max, -visc_mu(0.5f * (p.w + q.w), rv, r2, hp.eta));
         }
         const int oi = perm[i];
         if (e > b) dt = cfl_bound(C, hp, s_min, c_max, mu_max, acc_hyd[oi], grav[oi]);
