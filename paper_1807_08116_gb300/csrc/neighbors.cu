@@ -307,19 +307,21 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
 
 // Second half of the single-search build: copy each staged row into its CSR
 // place and append the row to the reverse part of every coarser partner
-// (rows on the overflow list are filled by NB_FILL_LISTED instead).  One warp
-// per row, lanes over its entries, so reads and writes are coalesced; the
-// search marked the coarser partners with the top bit of the staged index.
-constexpr int kCopyWarps = 8;
-__global__ void __launch_bounds__(kCopyWarps * 32) nb_copy_kernel(NbArgs a) {
-    const long long i = ((long long)blockIdx.x * kCopyWarps + (threadIdx.x >> 5));
-    const int lane = threadIdx.x & 31;
+// (rows on the overflow list are filled by NB_FILL_LISTED instead).
+// kCopyLanes lanes per row take its entries in turn, so a warp moves several
+// rows at once with coalesced reads and writes; the search marked the
+// coarser partners with the top bit of the staged index.
+constexpr int kCopyThreads = 256;
+constexpr int kCopyLanes = 8;
+__global__ void __launch_bounds__(kCopyThreads) nb_copy_kernel(NbArgs a) {
+    const long long i = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) / kCopyLanes;
+    const int sl = threadIdx.x % kCopyLanes;
     if (i >= a.n) return;
     const int cnt = a.own[i];
     if (cnt > a.stage_k) return;
     const long long base = a.nb_start[i];
     const int *row = a.stage + i * a.stage_k;
-    for (int c = lane; c < cnt; c += 32) {
+    for (int c = sl; c < cnt; c += kCopyLanes) {
         const int v = row[c];
         const int j = v & 0x7fffffff;
         const long long w = base + c;
@@ -353,7 +355,8 @@ int launch_nb_count(const NbArgs &a, cudaStream_t st) {
 int launch_nb_fill(const NbArgs &a, cudaStream_t st) {
     if (a.n > 0) {
         if (a.stage) {
-            nb_copy_kernel<<<(a.n + kCopyWarps - 1) / kCopyWarps, kCopyWarps * 32, 0, st>>>(a);
+            nb_copy_kernel<<<(unsigned)(((long long)a.n * kCopyLanes + kCopyThreads - 1) / kCopyThreads),
+                             kCopyThreads, 0, st>>>(a);
             nb_kernel<NB_FILL_LISTED><<<(a.n + 127) / 128, 128, 0, st>>>(a);
             note_launch(2);
         } else {

@@ -298,3 +298,18 @@ def test_row_layout_own_then_reverse_ascending(orc, n_wide):
         assert np.all(np.diff(row[len(row) - k:]) > 0), f"row {s}: reverse part not ascending"
     lens = np.array(lens)
     assert lens.max() > 64 and ((lens > 1) & (lens <= 32)).any() and ((lens > 32) & (lens <= 64)).any()
+
+
+def test_group_wider_than_one_row_cap_walks_row_by_row(orc):
+    # one level of cells of 1/64 and h = 0.994: each row's search box spans
+    # 255 cells per axis (16.6M cells, under the 2^24 cap of one row), but
+    # two rows 3 cells apart in every axis form one group whose union box
+    # spans 258 (17.2M cells, over the cap); the group is then walked row by
+    # row, and the lists must still be the brute-force ones, with no flag
+    x = np.float32(0.5 / 64)
+    ph = np.array([[x, x, x, 0.994], [x + 3 / 64, x + 3 / 64, x + 3 / 64, 0.994]], np.float32)
+    grid = dict(x0=-4.0, y0=-4.0, z0=-4.0, log2_L0=-6, n_levels=1, log2_M=10)
+    ctx = _ctx(2, log2_M=10)
+    ctx, perm = _check_sort(orc, ph, grid, ctx)
+    start, idx, sets = _check_lists(orc, ph, ctx, perm)
+    assert sets == {0: {1}, 1: {0}}
