@@ -530,6 +530,15 @@ def run_ensemble(args):
     for k, sm in enumerate(sims):
         r = sm.positions()
         worst = max(worst, float(np.abs(rb[bsim.sim_slices(k)] - r).max() / max(np.abs(r).max(), 1e-30)))
+    # stage breakdown of one more batched step (eager, outside the timed region,
+    # after the comparison of positions)
+    ev = nv.StageEvents()
+    bsim.state.events = ev.ptr
+    bsim.step(dt, check=False)
+    torch.cuda.synchronize()
+    bsim.state.events = None
+    stage_b = ev.stage_ms()
+    ev.close()
     v_b = n_tot * args.steps / (ms_b / 1e3)
     v_s = n_tot * args.steps / (ms_s / 1e3)
     line = {
@@ -545,6 +554,7 @@ def run_ensemble(args):
                                else "one-sided persistent work queue"),
                    "gravity_units_R": best_R, "autotune_ms": tune},
         "max_rel_position_diff_batched_vs_sequential": worst,
+        "stage_ms_batched": stage_b,
         "interactions_per_step": float(sum(d["n"] ** 2 for d in lst)),
     }
     print(json.dumps(line), flush=True)
