@@ -73,6 +73,19 @@ def tune_lanes(sim, reps=3):
     return best, res
 
 
+def pairs_crossover(res):
+    """The smallest size from which the pair-once time (res[n][1]) beats the
+    one-sided time (res[n][0]) at that and every larger measured size, or
+    None when it does not win at the largest."""
+    threshold = None
+    for n in sorted(res, reverse=True):
+        if res[n][1] < res[n][0]:
+            threshold = n
+        else:
+            break
+    return threshold
+
+
 def tune_pairs_threshold(make_pos_m, sizes=(8192, 12288, 16384, 24576, 32768, 49152, 65536),
                          G=1.0, eps=0.01, reps=5, apply=True):
     """Time the one-sided kernel (its cost-model plan) and the pair-once
@@ -92,12 +105,7 @@ def tune_pairs_threshold(make_pos_m, sizes=(8192, 12288, 16384, 24576, 32768, 49
             res[n] = (t1, t2)
     finally:
         nv.pp_gravity_pairs_min_n(0)
-    threshold = None
-    for n in sorted(res, reverse=True):
-        if res[n][1] < res[n][0]:
-            threshold = n
-        else:
-            break
+    threshold = pairs_crossover(res)
     if apply and threshold is not None:
         nv.pp_gravity_pairs_min_n(threshold)
     return threshold, res

@@ -81,3 +81,13 @@ def test_gravity_traffic_only_while_the_kernel_source_is_unchanged(monkeypatch):
     fake["pp_gravity_pairs_kernel"] = dict(rec, sha256="0" * 64)
     monkeypatch.setattr(bench, "GFC_TRAFFIC", fake)
     assert bench.gfc_traffic(rec["n"], "pp_gravity_pairs_kernel") is None
+
+
+def test_pairs_crossover_choice():
+    from paper_1807_08116_gb300.tune import pairs_crossover
+    # (one-sided ms, pair-once ms) per size
+    assert pairs_crossover({8192: (0.07, 0.15), 16384: (0.25, 0.21), 32768: (0.51, 0.38)}) == 16384
+    # a win below a loss does not count: the threshold is where the wins stay
+    assert pairs_crossover({8192: (0.2, 0.1), 16384: (0.2, 0.3), 32768: (0.5, 0.4)}) == 32768
+    assert pairs_crossover({8192: (0.1, 0.2), 16384: (0.2, 0.3)}) is None
+    assert pairs_crossover({}) is None
