@@ -15,9 +15,11 @@ consumes, promotes them exactly to FP64 and returns FP64 results.
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself: kernel normalisation and C^2 continuity (Eqs. 8-9), uniform-lattice
 density (Eq. 7), two-body and Plummer closed forms (Eq. 4), momentum and
-energy conservation of the pairwise forms (Eqs. 10-11), velocity-Verlet
-equivalence of the scheme for dark-only runs (Eqs. 12-16), and numpy's stable
-argsort / scipy's k-d tree for the binning and the neighbour sets.
+energy conservation of the pairwise forms (Eqs. 10-11), a hand-worked
+two-particle head-on case for the artificial viscosity (after Eq. 11),
+velocity-Verlet equivalence of the scheme for dark-only runs (Eqs. 12-16),
+and numpy's stable argsort / scipy's k-d tree for the binning and the
+neighbour sets.
 """
 from __future__ import annotations
 

@@ -115,6 +115,26 @@ def test_forces_at_rest_and_without_viscosity(orc):
     assert np.all(a[:, 3] == 0.0)
 
 
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_forces_head_on_pair_matches_hand_calculation(lanes):
+    # the two-particle head-on case worked by hand from the definitions of
+    # Pi_ij, nu_ij and mu_ij (Sect. 2.2), in FP32 on the device
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "viscosity_head_on.json")) as f:
+        g = json.load(f)
+    ph = np.array(g["pos_h"], np.float32)
+    ve = np.array(g["vel_e"], np.float32)
+    mass = np.array(g["mass"], np.float32)
+    rho = np.array(g["rho"], np.float32)
+    a = _forces(ph, ve, mass, rho, lanes, gamma=g["gamma"], alpha=g["alpha"], beta=g["beta"],
+                eta=g["eta"])
+    acc, de = np.array(g["acc"]), np.array(g["dedt"])
+    assert np.abs(a[:, :3] - acc).max() < 2e-6 * np.abs(acc).max()
+    assert np.abs(a[:, 3] - de).max() < 2e-6 * np.abs(de).max()
+
+
 def test_two_halo_sampled_rows(orc):
     d = ics.two_halo(131072, 131072, seed=1)
     ph, mass, ve = _stirred(d, seed=1)
