@@ -52,9 +52,31 @@ GFC_TRAFFIC = {
     "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 2.35e9,
                                 "sha256": "b5c0566ea52f23c4381a2c4a8f339e9d4e21c5906cb11e593e76220d85b40914"},
 }
-# FP32 pipe of GB300: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz max clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
+FP32_LANES_PER_SM = 128      # FP32 lanes per SM on Blackwell (4 partitions x 32)
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def sm_max_mhz(clk=None):
+    """Maximum SM clock: the one nvidia-smi reported while the step ran, else
+    the pool's measured record, else GB300's nominal 2070 MHz."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        return SM_MAX_MHZ_FALLBACK
+
+
+def fp32_lane_ops_per_s(sm_count, mhz):
+    """FP32 pipe issue rate: SMs x 128 lanes x clock (one operation per lane
+    per clock; an FMA counts as 2 flop)."""
+    return sm_count * FP32_LANES_PER_SM * mhz * 1e6
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    return 2.0 * fp32_lane_ops_per_s(sm_count, mhz) / 1e12
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -127,7 +149,6 @@ def stage_roofline(stage_ms, n, ng, nb_entries):
 # per unordered pair (3 FADD, 3 FFMA, 4 FMUL, 2 x 3 FFMA), i.e. 8 per
 # ordered interaction.
 FP32_OPS = {"pp_gravity_kernel": 12, "pp_gravity_pairs_kernel": 8}
-FP32_LANE_OPS_PER_S = 152 * 128 * 2.07e9
 
 
 def make_ic(name, rank=0):
@@ -249,6 +270,27 @@ def oracle_sample(ic, rows_grav=256, rows_gas=256, seed=0):
             f"brute force FP64, extrapolated to one step; integrator over all particles; "
             f"sampled {t_grav + t_dc + t_hfc + t_su:.1f} s")
     return n / t_step, t_step, threads, desc
+
+
+def gravity_parity(sim, n_rows=64, seed=11):
+    """Accelerations of the last gravity evaluation on sampled rows against the
+    FP64 oracle over all sources at the same FP32 positions: rms relative
+    error, the maximum relative error with the 1% rms floor of the tests, and
+    the plain maximum |da_i| / |a_i|."""
+    import oracle
+    pm = sim.t["pos_m"].cpu().numpy()
+    g = sim.t["grav"][:, :3].cpu().numpy().astype(np.float64)
+    n = pm.shape[0]
+    rows = np.sort(np.random.default_rng(seed).choice(n, min(n_rows, n), replace=False)).astype(np.int32)
+    ref, _ = oracle.gravity(pm, sim.params["G"], sim.params["eps"], rows=rows)
+    d = np.linalg.norm(g[rows] - ref, axis=1)
+    nr = np.linalg.norm(ref, axis=1)
+    rms_ref = float(np.sqrt(np.mean(nr ** 2)))
+    return {"rows": int(len(rows)), "rms_rel": float(np.sqrt((d ** 2).sum() / (nr ** 2).sum())),
+            "max_rel_floored": float(np.max(d / (nr + 0.01 * rms_ref))),
+            "max_rel_plain": float(np.max(d / nr)),
+            "note": "gravity of the final timed state on sampled rows vs the FP64 oracle over all "
+                    "sources; floor = 1% of the rms |a| (the tests' metric)"}
 
 
 def run_reference(args):
@@ -385,15 +427,24 @@ def run_ours(args):
         kernel = "pp_gravity_kernel"
         R, S = nv.sph_gravity_plan(n)
         plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS,
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz_max = sm_max_mhz(clk)
+    mhz_run = float(clk["sm_mhz"]) if clk and clk.get("sm_mhz") else mhz_max
+    peak = fp32_peak_tflops(sms, mhz_max)
+    peak_run = fp32_peak_tflops(sms, mhz_run)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
             "traffic": args.gfc_traffic if args.gfc_traffic is not None else gfc_traffic(n, kernel),
             "kernel": kernel, "interactions_per_s": ips,
             "flop_per_interaction": FLOP_PER_INTERACTION,
             "fp32_ops_per_interaction": FP32_OPS[kernel],
-            "fp32_pipe_frac": FP32_OPS[kernel] * ips / FP32_LANE_OPS_PER_S,
-            "peak_note": "FP32 pipe 152 SM x 128 lanes x 2 flop x 2.07 GHz (derived, not measured); "
-                         "achieved counts 20 flop per ordered interaction (N^2 per evaluation)",
+            "fp32_pipe_frac": FP32_OPS[kernel] * ips / fp32_lane_ops_per_s(sms, mhz_max),
+            "sm_count": sms, "sm_max_mhz": mhz_max, "sm_mhz": mhz_run,
+            "peak_at_sm_mhz": peak_run, "frac_at_sm_mhz": achieved / peak_run,
+            "peak_note": f"FP32 pipe {sms} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz_max:.0f} MHz "
+                         "(the device's SM count and maximum SM clock; derived, not measured); "
+                         "achieved counts 20 flop per ordered interaction (N^2 per evaluation); "
+                         "frac_at_sm_mhz takes the median SM clock sampled during the timed steps",
             "plan": plan}
 
     cpu = None
@@ -410,6 +461,8 @@ def run_ours(args):
         finally:
             oracle.set_threads(threads)
         cpu["single_thread"] = {"value": v1, "cores": threads1, "sample": desc1}
+        # the sampled oracle rows double as a parity check of the timed state
+        cpu["gravity_parity"] = gravity_parity(sim)
 
     if rank == 0:
         line = {
@@ -445,7 +498,7 @@ def run_e2e(sim, args, dt, barrier, dist, world, n, ng):
     torch.cuda.synchronize()
     h2d = sum(host[k].numel() * host[k].element_size() for k in ("r", "v", "e", "h"))
     d2h = sum(host[k].numel() * host[k].element_size() for k in ("r", "v", "e"))
-    steps = max(1, min(args.steps, args.e2e_steps))
+    steps = max(1, args.e2e_steps if args.e2e_steps is not None else args.steps)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -661,12 +714,14 @@ def run_gravity(args):
     else:
         R, S = nv.sph_gravity_plan(n)
         plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz()
     print(json.dumps({"metric": "PP interactions/s", "value": ips, "unit": "interactions/s",
                       "n": n, "ms_per_launch": ms, "steps": args.steps, "warmup": args.warmup,
                       "kernel": kernel, "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12,
-                      "frac_of_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / FP32_PEAK_TFLOPS,
-                      "fp32_pipe_frac": FP32_OPS[kernel] * ips / FP32_LANE_OPS_PER_S,
-                      "plan": plan}), flush=True)
+                      "frac_of_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / fp32_peak_tflops(sms, mhz),
+                      "fp32_pipe_frac": FP32_OPS[kernel] * ips / fp32_lane_ops_per_s(sms, mhz),
+                      "sm_count": sms, "sm_max_mhz": mhz, "plan": plan}), flush=True)
     return 0
 
 
@@ -689,7 +744,8 @@ def main(argv=None):
     ap.add_argument("--conservation", action="store_true",
                     help="report the energy and momentum change over the timed steps")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end measurement (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=512,
                     help="target rows per stage of each reference-arm step sample")

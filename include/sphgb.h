@@ -150,10 +150,14 @@ int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_gas,
  * copy is kept).  Limits: n_gas <= SPH_NOALLOC_MAX_GAS and log2_M <=
  * SPH_NOALLOC_MAX_LOG2_M, else SPH_ERR_INVALID_ARG before anything runs.
  * h_grid == NULL derives the grid on the device as sph_bin_and_sort does.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents: calls whose
- * work may overlap on the GPU race on it, so order them (one stream). */
+ * Every call looks up the array's device address with the caller's device
+ * current (cudaGetSymbolAddress, a host call that allocates nothing), so a
+ * device reset or another context never leaves it a stale address; the
+ * first call on a device may load the library's device code, so make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (the call clears what must start at zero):
+ * calls whose work may overlap on the GPU race on it, so order them (one
+ * stream). */
 #define SPH_NOALLOC_MAX_GAS 65536
 #define SPH_NOALLOC_MAX_LOG2_M 17
 #define SPH_NOALLOC_SCRATCH_BYTES 2097152
@@ -291,6 +295,22 @@ int pp_gravity_pairs_min_n(int32_t n_min);
 /* Synchronise `stream`, read and clear the gravity kernel's device status
  * word (SPH_FLAG_TIMEOUT).  Returns SPH_ERR_DEVICE if a bit was set. */
 int pp_gravity_status(sph_stream_t stream, int32_t *h_flags);
+
+/* Failure detection (no counterpart in the paper).  Every mbarrier wait of
+ * the TMA-fed gravity kernels is bounded in time: a wait that runs out sets
+ * SPH_FLAG_TIMEOUT in the gravity status word, the block waits (within the
+ * same limit) for the copies it still has in flight and returns, so the
+ * CUDA context stays usable and the host reads the failure through
+ * pp_gravity_status.  sph_set_wait_limit_ns sets that limit for every later
+ * launch on the current device (process-wide; 1 us .. 60 s; 0 restores the
+ * default of 2 s; a synchronous host call). */
+int sph_set_wait_limit_ns(int64_t limit_ns);
+
+/* Probe of the timeout path: one block runs the bounded wait on an mbarrier
+ * that expects 16 bytes no copy will bring, so the wait runs out after the
+ * limit, SPH_FLAG_TIMEOUT is recorded and the kernel returns.  Nothing is
+ * read or written but the status word; no copy is issued. */
+int sph_wait_probe(sph_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Stage SU: leapfrog predictor-corrector (Eqs. 12-16).                      */

@@ -19,6 +19,14 @@ using namespace sphgb;
 namespace sphgb {
 static std::atomic<long long> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int device_num_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    return sms;
+}
 }  // namespace sphgb
 
 extern "C" int64_t sph_launch_count(void) { return g_launches.load(); }

@@ -1,6 +1,7 @@
 // async.cuh -- inline-PTX helpers shared by the gravity kernels: mbarrier
 // phases, 1-D TMA bulk copies global -> shared, a time-bounded mbarrier wait
-// (%globaltimer), and the MUFU reciprocal square root.
+// (%globaltimer, limit read from device memory), and the MUFU reciprocal
+// square root.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,13 +39,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+// Wait for phase `parity` of an mbarrier, giving up after *limit_ns
+// nanoseconds of %globaltimer (the limit is read only once the first test
+// has failed, so the common case costs one try_wait).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
+                                                  const unsigned long long *limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
-    unsigned long long t0 = global_ns();
+    const unsigned long long lim = *reinterpret_cast<const volatile unsigned long long *>(limit_ns);
+    const unsigned long long t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > lim) return false;
     }
 }
 

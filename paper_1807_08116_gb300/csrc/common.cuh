@@ -124,6 +124,9 @@ __device__ __forceinline__ void set_flag(int *flags, int bit) {
 
 // Count kernel launches made by the library (read through sph_launch_count).
 void note_launch(int k = 1);
+
+// Streaming multiprocessors of the current device (152 on GB300).
+int device_num_sms();
 }  // namespace sphgb
 
 // Host-side launch helpers shared by the translation units.

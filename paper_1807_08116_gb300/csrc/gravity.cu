@@ -61,6 +61,19 @@ constexpr int GR_SMEM_RED = 4 * GR_THREADS * 8 * 4;
 constexpr int GR_SMEM = (GR_SMEM_TILES > GR_SMEM_RED ? GR_SMEM_TILES : GR_SMEM_RED) + 64;
 
 __device__ int g_grav_flags;
+// time limit of every bounded mbarrier wait (sph_set_wait_limit_ns)
+constexpr unsigned long long kWaitLimitDefaultNs = 2000000000ull;
+__device__ unsigned long long g_wait_limit_ns = kWaitLimitDefaultNs;
+
+// After a wait gave up: the tiles [t, t_end) were issued and not consumed, so
+// their copies may still be landing in this block's shared memory; thread 0
+// waits for each of them, again within the limit, before the block exits.
+__device__ __forceinline__ void drain_tiles(unsigned bar0, unsigned t, unsigned t_end, int nbuf) {
+    if (threadIdx.x == 0)
+        for (unsigned u = t; u < t_end; ++u)
+            mbar_wait_bounded(bar0 + 8 * (u % nbuf), (u / nbuf) & 1u, &g_wait_limit_ns);
+    __syncthreads();
+}
 
 // Expand a landed tile (x, y, z, m) into duplicated pairs ((x, x, y, y),
 // (z, z, m, m)), one per source.
@@ -205,8 +218,12 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
     bool failed = false;
     for (int t = 0; t < my_tiles; ++t) {
         const int buf = t % GR_NBUF;
-        bool ok = mbar_wait_bounded(bar0 + 8 * buf, (unsigned)((t / GR_NBUF) & 1));
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        bool ok = mbar_wait_bounded(bar0 + 8 * buf, (unsigned)((t / GR_NBUF) & 1), &g_wait_limit_ns);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            drain_tiles(bar0, t, min(my_tiles, t + GR_NBUF), GR_NBUF);
+            break;
+        }
         const int cnt = min(GR_TJ, n - (t_begin + t) * GR_TJ);
         const float4 *tb = tiles + buf * GR_TJ;
         expand_tile(tb, dup, cnt);
@@ -350,8 +367,12 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
         for (int t = 0; t < nt; ++t) {
             const unsigned q = seq + t;
             const int buf = q % GR_NBUF;
-            bool ok = mbar_wait_bounded(bar0 + 8 * buf, (q / GR_NBUF) & 1u);
-            if (__syncthreads_or(!ok)) { failed = true; break; }
+            bool ok = mbar_wait_bounded(bar0 + 8 * buf, (q / GR_NBUF) & 1u, &g_wait_limit_ns);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                drain_tiles(bar0, q, seq + min(nt, t + GR_NBUF), GR_NBUF);
+                break;
+            }
             const int cnt = min(GR_TJ, ns - t * GR_TJ);
             expand_tile(tiles + buf * GR_TJ, dup, cnt);
             __syncthreads();
@@ -570,19 +591,12 @@ int gravity_num_sms() {
     return g_num_sms;
 }
 
+// Looked up on every call: an address kept from an earlier call would belong
+// to the context it was taken in (stale after a device reset).
 int *gravity_flags_device() {
-    constexpr int kMaxDevices = 64;
-    static int *ptr[kMaxDevices];
-    static std::mutex m;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(m);
-    if (!ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_grav_flags) != cudaSuccess) return nullptr;
-        ptr[dev] = static_cast<int *>(p);
-    }
-    return ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_grav_flags) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
 }
 
 bool gravity_plan_forced() { return g_force_R.load() != 0; }
@@ -670,6 +684,39 @@ extern "C" int pp_gravity_status(sph_stream_t stream, int32_t *h_flags) {
     SPH_CUDA_TRY(cudaMemcpyToSymbol(g_grav_flags, &zero, sizeof(int)));
     *h_flags = v;
     return v ? SPH_ERR_DEVICE : SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Failure detection: the time limit of the bounded waits, and a probe that
+// makes one such wait run out.
+// ---------------------------------------------------------------------------
+
+// One arrival with 16 bytes of expected transaction that no copy will bring:
+// the phase cannot complete, the bounded wait gives up after the limit, the
+// status word records it and the block returns.  No copy is ever issued, so
+// nothing is in flight when it exits.
+__global__ void wait_probe_kernel() {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const unsigned b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(b, 16u);
+    if (!mbar_wait_bounded(b, 0u, &g_wait_limit_ns)) atomicOr(&g_grav_flags, SPH_FLAG_TIMEOUT);
+}
+
+extern "C" int sph_set_wait_limit_ns(int64_t limit_ns) {
+    if (limit_ns != 0 && (limit_ns < 1000 || limit_ns > 60000000000ll)) return SPH_ERR_INVALID_ARG;
+    const unsigned long long v = limit_ns ? (unsigned long long)limit_ns : kWaitLimitDefaultNs;
+    SPH_CUDA_TRY(cudaMemcpyToSymbol(g_wait_limit_ns, &v, sizeof(v)));
+    return SPH_OK;
+}
+
+extern "C" int sph_wait_probe(sph_stream_t stream) {
+    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>();
+    note_launch();
+    SPH_LAUNCH_CHECK();
+    return SPH_OK;
 }
 
 // Launch plan exposed for tests and the bench's roofline accounting.

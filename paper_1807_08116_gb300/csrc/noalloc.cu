@@ -15,8 +15,6 @@
 // All calls on a device share it and it keeps the last call's contents, so
 // two calls whose work overlaps on the GPU (different streams, no ordering
 // between them) race on it; order them, e.g. issue them on one stream.
-#include <mutex>
-
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -43,23 +41,16 @@ static_assert(kNaBytes <= SPH_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SPH_NOALLOC_SCRATCH_BYTES];
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side name of the array is not a device address).
-constexpr int kNaMaxDevices = 64;
-static unsigned char *g_na_ptr[kNaMaxDevices];
-static std::mutex g_na_mutex;
-
+// Device address of the scratch array.  The host-side name of the array is
+// not a device address, so it is looked up with the caller's device current.
+// The lookup is repeated on every call (a cheap host call): an address kept
+// from an earlier call would belong to the context it was taken in, and is
+// stale after cudaDeviceReset or under another context on the same device.
 static int noalloc_scratch(unsigned char **out) {
-    int dev = 0;
-    SPH_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNaMaxDevices) return SPH_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        SPH_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_na_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_na_ptr[dev];
+    void *p = nullptr;
+    SPH_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!p) return SPH_ERR_CUDA;
+    *out = static_cast<unsigned char *>(p);
     return SPH_OK;
 }
 

@@ -168,7 +168,13 @@ struct sph_server {
 
 namespace {
 
+// Give the job's memory back to the arena.  Kernels of the job may still be
+// queued on its stream (the list build of size_lists, a step that failed on
+// the host side after launching work), and the arena may hand the same bytes
+// to another job on another stream at once, so the stream is drained first.
 void free_device(sph_server *s, Job &j) {
+    if ((j.has_ws || j.has_state) && !s->streams.empty())
+        cudaStreamSynchronize(s->streams[j.stream_slot]);
     if (j.ctx) {
         sph_ctx_destroy(j.ctx);
         j.ctx = nullptr;
@@ -198,7 +204,16 @@ int make_ctx(sph_server *s, Job &j, long long capacity, cudaStream_t st) {
         return rc;
     }
     if (j.ctx) sph_ctx_destroy(j.ctx);
-    if (j.has_ws) s->arena.release(j.ws_off, j.ws_bytes);
+    if (j.has_ws) {
+        // the old workspace may still be read by work queued on st
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            sph_ctx_destroy(c);
+            s->arena.release(off, need);
+            j.ctx = nullptr;
+            return SPH_ERR_CUDA;
+        }
+        s->arena.release(j.ws_off, j.ws_bytes);
+    }
     j.ctx = c;
     j.ws_off = off;
     j.ws_bytes = need;
@@ -262,9 +277,9 @@ void admit_queued(sph_server *s) {
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->resident.size() < s->max_resident;) {
         Job &j = s->jobs[*it];
         const int slot = (int)(j.id % s->streams.size());
+        j.stream_slot = slot;
         int rc = admit(s, j, s->streams[slot]);
         if (rc == SPH_OK) {
-            j.stream_slot = slot;
             s->resident.push_back(j.id);
             it = s->queue.erase(it);
         } else if (rc == SPH_ERR_BUDGET && !s->resident.empty()) {

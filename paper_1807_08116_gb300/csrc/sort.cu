@@ -522,7 +522,8 @@ int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, Grid
     const unsigned init[5] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu, 0u};
     // red is reset by a tiny kernel so the sequence stays capturable
     grid_reset_red(red, init, st);
-    unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4 * 152);
+    // a few resident blocks per SM of this device, each striding over the input
+    unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4u * (unsigned)device_num_sms());
     if (n > 0) grid_reduce_kernel<<<nb, 256, 0, st>>>(pos_h, n, red);
     grid_finalize_kernel<<<1, 32, 0, st>>>(red, log2_M, grid);
     note_launch(n > 0 ? 3 : 2);

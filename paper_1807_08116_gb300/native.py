@@ -126,6 +126,8 @@ def lib():
             "sph_cfl_dt": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
             "pp_gravity": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "pp_gravity_status": (_I, [_P, ctypes.POINTER(_I)]),
+            "sph_set_wait_limit_ns": (_I, [_I64]),
+            "sph_wait_probe": (_I, [_P]),
             "pp_gravity_pairs": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P,
                                       ctypes.c_size_t, _P]),
             "pp_gravity_pairs_workspace_bytes": (ctypes.c_size_t, [_I]),
@@ -391,6 +393,16 @@ def pp_gravity_status(stream=None):
     if rc not in (SPH_OK, SPH_ERR_DEVICE):
         _check("pp_gravity_status", rc)
     return int(f.value)
+
+
+def sph_set_wait_limit_ns(limit_ns=0):
+    """Time limit of the gravity kernels' bounded waits (0: the default 2 s)."""
+    _check("sph_set_wait_limit_ns", lib().sph_set_wait_limit_ns(int(limit_ns)))
+
+
+def sph_wait_probe(stream=None):
+    """Launch the probe whose bounded wait runs out (sets SPH_FLAG_TIMEOUT)."""
+    _check("sph_wait_probe", lib().sph_wait_probe(_stream(stream)))
 
 
 def sph_gravity_plan(n, flags=0):

@@ -5,7 +5,7 @@ one-sided kernel, and whole simulations that take the pair-once path."""
 import numpy as np
 import pytest
 
-from helpers import MAX_TOL, RMS_TOL, err, need_gpu, pos_m_of
+from helpers import MAX_TOL, RMS_TOL, err, max_plain, need_gpu, pos_m_of
 from paper_1807_08116_gb300 import ics
 
 pytestmark = pytest.mark.gpu
@@ -85,7 +85,8 @@ def test_single_halo_all_rows_and_momentum(orc, low_threshold):
     g = _pairs(pm, flags=nv.SPH_GRAV_POTENTIAL)
     acc, pot = orc.gravity(pm)
     rms, mx = err(g[:, :3], acc)
-    print(f"pairs 16384: rms {rms:.2e} max {mx:.2e}")
+    print(f"pairs 16384: rms {rms:.2e} max {mx:.2e} (plain max "
+          f"{max_plain(g[:, :3], acc):.2e})")
     assert rms <= RMS_TOL and mx <= MAX_TOL
     prms, pmx = err(g[:, 3:], pot[:, None])
     assert prms <= RMS_TOL and pmx <= MAX_TOL
@@ -148,7 +149,8 @@ def test_two_halo_sampled_rows(orc):
     rows = np.random.default_rng(0).choice(len(pm), 512, replace=False)
     acc, pot = orc.gravity(pm, rows=rows)
     rms, mx = err(g[rows, :3], acc)
-    print(f"pairs 524288 sample: rms {rms:.2e} max {mx:.2e}")
+    print(f"pairs 524288 sample: rms {rms:.2e} max {mx:.2e} (plain max "
+          f"{max_plain(g[rows, :3], acc):.2e})")
     assert rms <= RMS_TOL and mx <= MAX_TOL
     prms, pmx = err(g[rows, 3:], pot[:, None])
     assert prms <= RMS_TOL and pmx <= MAX_TOL
@@ -163,8 +165,22 @@ def test_large_collision_sampled_rows(orc):
     rows = np.random.default_rng(1).choice(len(pm), 256, replace=False)
     acc, _ = orc.gravity(pm, rows=rows)
     rms, mx = err(g[rows, :3], acc)
-    print(f"pairs 4194304 sample: rms {rms:.2e} max {mx:.2e}")
+    print(f"pairs 4194304 sample: rms {rms:.2e} max {mx:.2e} (plain max "
+          f"{max_plain(g[rows, :3], acc):.2e})")
     assert rms <= RMS_TOL and mx <= MAX_TOL
+    # the one-sided kernel (per-tile Kahan sums) on the same rows, for the
+    # record: the pair-once kernel's in-tile sums are plain FP32, its sums
+    # across tiles exact in fixed point
+    torch = need_gpu()
+    x = torch.as_tensor(pm, device="cuda")
+    o = torch.empty_like(x)
+    nv.pp_gravity(x, o)
+    torch.cuda.synchronize()
+    g1 = o.cpu().numpy().astype(np.float64)
+    rms1, mx1 = err(g1[rows, :3], acc)
+    print(f"one-sided (Kahan) 4194304 same rows: rms {rms1:.2e} max {mx1:.2e} (plain max "
+          f"{max_plain(g1[rows, :3], acc):.2e})")
+    assert rms1 <= RMS_TOL and mx1 <= MAX_TOL
 
 
 def test_simulation_takes_pair_path(orc):

@@ -88,3 +88,83 @@ def test_budget_admission_and_errors():
     srv.release(ids[0])
     with pytest.raises(nv.SphError):
         srv.poll(ids[0])
+
+
+def test_job_admitted_mid_stream_matches_the_oracle(orc):
+    # a collision submitted while another job is already running, advanced in
+    # the mix, against the FP64 oracle stepping the same initial condition
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server
+    from helpers import err
+    x = ics.two_halo(1024, 1024, seed=48)
+    busy = ics.single_halo(3000, 1500, seed=49)
+    srv = Server(1 << 30, max_resident=4, n_streams=2)
+    jb = srv.submit(busy, 8)
+    srv.step()
+    srv.step()
+    jx = srv.submit(x, 5)
+    _run_all(srv)
+    got = srv.poll(jx, with_result=True)
+    assert got["state"] == nv.SIM_DONE and got["steps_done"] == 5
+    assert srv.poll(jb)["state"] == nv.SIM_DONE
+    ref = orc.OracleSim(x["r"].T, x["v"].T, x["e"], x["m"], x["h"], x["n_gas"])
+    ref.initial_rhs()
+    for _ in range(5):
+        ref.step(1e-3)
+    dr = np.abs(got["r"] - ref.r.T).max()
+    rv, mv = err(got["v"], ref.v.T)
+    re_, _ = err(got["e"][:, None], ref.e[:, None])
+    print(f"served job vs oracle: |dr| {dr:.2e}, v rms {rv:.2e} max {mv:.2e}, e rms {re_:.2e}")
+    assert dr < 1e-9
+    assert rv < 1e-6
+    assert re_ < 1e-6
+
+
+def _scaled_h_job(orc, n_gas, lo, hi, seed):
+    """A gas sphere whose smoothing lengths are scaled so that its neighbour
+    lists need between lo and hi entries per particle (brute-force count)."""
+    from helpers import pos_h_of
+    d = ics.single_halo(n_gas, 0, seed=seed)
+    for f in np.linspace(1.0, 1.6, 25):
+        h = (d["h"] * f).astype(np.float32)
+        starts, _ = orc.neighbors(pos_h_of(d["r"], h))
+        per = starts[-1] / n_gas
+        if lo < per < hi:
+            d = dict(d)
+            d["h"] = h
+            return d, per
+    raise AssertionError("no scale puts the list length in range")
+
+
+def test_admission_that_fails_after_sizing_lists_leaves_the_next_job_intact(orc):
+    # The first job's lists need 88-115 entries per particle: admission builds
+    # them in its first context (120 per particle), finds them more than 70%
+    # full, and asks the arena for a larger context, which the budget refuses.
+    # Its memory goes back to the arena while its list kernels may still be
+    # queued; the next job is admitted into the same bytes on another stream
+    # and must still give exactly its lone result.
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server
+    big, per = _scaled_h_job(orc, 6000, 88.0, 115.0, seed=50)
+    small = ics.single_halo(1500, 500, seed=51)
+    alone = Server(256 << 20, max_resident=2, n_streams=2)
+    js = alone.submit(small, 3)
+    _run_all(alone)
+    ref = alone.poll(js, with_result=True)
+    assert ref["state"] == nv.SIM_DONE
+    # an arena that holds the big job's state and first context, not a second one
+    ws1 = nv.sph_ctx_workspace_bytes(6000, nv.default_log2_M(6000), 120 * 6000)
+    budget = int(1.3 * ws1) + (4 << 20)
+    srv = Server(budget, max_resident=2, n_streams=2)
+    jf = srv.submit(big, 3)
+    jn = srv.submit(small, 3)
+    _run_all(srv)
+    st = srv.poll(jf)
+    assert st["state"] == nv.SIM_FAILED and st["error"] == nv.SPH_ERR_BUDGET, (st, per)
+    got = srv.poll(jn, with_result=True)
+    assert got["state"] == nv.SIM_DONE
+    for k in ("r", "v", "e"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert srv.info()["arena_free_bytes"] == srv.info()["arena_bytes"]

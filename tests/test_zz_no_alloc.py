@@ -1,5 +1,6 @@
 """The allocation-free grid sort (sph_bin_and_sort_noalloc) against the
-context-based sph_bin_and_sort.
+context-based sph_bin_and_sort and against the oracle's binning and stable
+counting sort, bit for bit.
 
 The allocation-free entry point exists for callers that cannot allocate
 device memory (a framework that owns all device memory, a plugin given only
@@ -9,6 +10,8 @@ it fails, a run that stops at the first failure has already run every other
 test.
 """
 import ctypes
+import os
+import re
 
 import numpy as np
 import pytest
@@ -17,6 +20,16 @@ from helpers import need_gpu, pos_h_of
 from paper_1807_08116_gb300 import ics
 
 pytestmark = pytest.mark.gpu
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "sphgb.h")
+
+
+def _limit(name):
+    """A limit as the public header states it."""
+    with open(HEADER) as f:
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", f.read())
+    return int(m.group(1))
 
 
 def _entry():
@@ -45,7 +58,7 @@ def _noalloc_sort(ph, log2_M, grid=None):
     return key.cpu().numpy(), start.cpu().numpy(), perm.cpu().numpy()
 
 
-def _context_sort(ph, log2_M, grid=None):
+def _context_sort(ph, log2_M, grid=None, want_grid=False):
     torch = need_gpu()
     from paper_1807_08116_gb300 import native as nv
     n = len(ph)
@@ -56,10 +69,18 @@ def _context_sort(ph, log2_M, grid=None):
     nv.sph_bin_and_sort(ctx, torch.as_tensor(ph, device="cuda"), grid=grid, key=key,
                         cell_start=start, perm=perm)
     torch.cuda.synchronize()
-    return key.cpu().numpy(), start.cpu().numpy(), perm.cpu().numpy()
+    out = (key.cpu().numpy(), start.cpu().numpy(), perm.cpu().numpy())
+    return (out, ctx.grid()) if want_grid else out
 
 
-def test_noalloc_sort_equals_context_sort_twice_in_a_row():
+def _oracle_sort(orc, ph, grid):
+    # the plain definition: bin every particle, then a stable counting sort
+    _, _, key = orc.bin_particles(ph, grid)
+    _, start, perm = orc.counting_sort(key, 1 << grid["log2_M"])
+    return key, start, perm
+
+
+def test_noalloc_sort_equals_context_sort_twice_in_a_row(orc):
     # two different particle sets back to back: the second call must not see
     # anything the first one left in the shared scratch array
     a = ics.single_halo(8192, 0, seed=11)
@@ -78,6 +99,33 @@ def test_noalloc_sort_equals_context_sort_twice_in_a_row():
     again = _noalloc_sort(ph_a, 14)
     for g, r in zip(again, ref_a):
         assert np.array_equal(g, r)
+    # and directly against the oracle's binning and stable counting sort
+    for g, o in zip(got_b, _oracle_sort(orc, ph_b, grid_b)):
+        assert np.array_equal(g, o)
+
+
+def test_noalloc_sort_at_its_largest_size(orc):
+    # n_gas and 2^log2_M both at the stated limits with a derived grid: every
+    # part of the fixed scratch layout is used at its largest extent
+    d = ics.two_halo(32768, 0, seed=13)
+    ph = pos_h_of(d["r"], d["h"])
+    assert len(ph) == _limit("SPH_NOALLOC_MAX_GAS") == 65536
+    log2_M = _limit("SPH_NOALLOC_MAX_LOG2_M")
+    got = _noalloc_sort(ph, log2_M)
+    ref, g = _context_sort(ph, log2_M, want_grid=True)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    for a, b in zip(got, _oracle_sort(orc, ph, g)):
+        assert np.array_equal(a, b)
+    # a second call on other data, then the first again: nothing carries over
+    o = ics.single_halo(40000, 0, seed=14)
+    other = pos_h_of(o["r"], o["h"])
+    got_o = _noalloc_sort(other, log2_M)
+    for a, b in zip(got_o, _context_sort(other, log2_M)):
+        assert np.array_equal(a, b)
+    again = _noalloc_sort(ph, log2_M)
+    for a, b in zip(again, ref):
+        assert np.array_equal(a, b)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
@@ -85,5 +133,6 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     from paper_1807_08116_gb300 import native as nv
     f = _entry()
     # checked on the host before any launch: no buffers are touched
-    assert f(None, 65537, 17, None, None, None, None, None) == nv.SPH_ERR_INVALID_ARG
-    assert f(None, 10, 18, None, None, None, None, None) == nv.SPH_ERR_INVALID_ARG
+    n_max, m_max = _limit("SPH_NOALLOC_MAX_GAS"), _limit("SPH_NOALLOC_MAX_LOG2_M")
+    assert f(None, n_max + 1, m_max, None, None, None, None, None) == nv.SPH_ERR_INVALID_ARG
+    assert f(None, 10, m_max + 1, None, None, None, None, None) == nv.SPH_ERR_INVALID_ARG
