@@ -254,6 +254,18 @@ int sph_forces_cfl(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const floa
 int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
                int32_t flags, sph_stream_t stream);
 
+/* The rows [i0, i1) of pp_gravity: g_i (and phi_i) of the targets i0 <= i <
+ * i1 over all n sources of d_pos_m[n][4], written to d_acc_pot[(i1 - i0)][4]
+ * (row i at d_acc_pot[i - i0]).  This is the per-GPU share of the paper's
+ * particle partition (Sect. 3: each of k GPUs computes the dynamics of N/k
+ * particles): a GPU that owns the rows [i0, i1) and has gathered every
+ * particle's (x, y, z, m) computes the gravity of its own particles.  The
+ * same one-sided kernel and summation order as pp_gravity: with the plan
+ * fixed by sph_gravity_tune(R, 1) the rows are bitwise those of pp_gravity.
+ * 0 <= i0 <= i1 <= n; i0 == i1 is a no-op. */
+int pp_gravity_rows(const float *d_pos_m, int32_t n, int32_t i0, int32_t i1, float G,
+                    float eps, float *d_acc_pot, int32_t flags, sph_stream_t stream);
+
 /* Launch plan pp_gravity uses for n particles and `flags`: *h_R targets per
  * thread (256 R per CTA, R in {2, 4, 8}; pairs of targets share packed FP32x2
  * instructions) and the cluster split *h_S of the source range. */

@@ -168,8 +168,8 @@ __device__ __forceinline__ void fold_tile(Kahan (&ax)[2 * RP], Kahan (&ay)[2 * R
 // straight from two broadcast 16-byte shared loads.
 template <int RP, bool POT, bool GUARD, bool KAHAN>
 __global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : SPHGB_GR_MINB)
-pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, float G, float eps2,
-                  float4 *__restrict__ out) {
+pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int n_tiles, int S,
+                  float G, float eps2, float4 *__restrict__ out) {
     constexpr int R = 2 * RP;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *tiles = reinterpret_cast<float4 *>(smem);            // [GR_NBUF][GR_TJ] raw
@@ -177,7 +177,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + GR_SMEM - 64);
     const int tid = threadIdx.x;
     const int rank = blockIdx.x % S;   // cluster dims (S, 1, 1): rank == ctarank
-    const int i0 = (blockIdx.x / S) * (GR_THREADS * R);
+    // targets [t0, t_end) of the n sources; target i is written to out[i - t0]
+    const int i0 = t0 + (blockIdx.x / S) * (GR_THREADS * R);
     const int t_begin = (int)((long long)n_tiles * rank / S);
     const int t_end = (int)((long long)n_tiles * (rank + 1) / S);
     const int my_tiles = t_end - t_begin;
@@ -188,8 +189,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
         int ia = i0 + tid + (2 * p) * GR_THREADS, ib = ia + GR_THREADS;
-        float4 a = ia < n ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 b = ib < n ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 a = ia < t_end ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 b = ib < t_end ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
         nx[p] = make_float2(-a.x, -b.x);
         ny[p] = make_float2(-a.y, -b.y);
         nz[p] = make_float2(-a.z, -b.z);
@@ -250,10 +251,10 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             int i = i0 + tid + k * GR_THREADS;
-            if (i < n) {
+            if (i < t_end) {
                 float pot = POT ? -G * (ph[k].s - ph[k].c) : 0.f;
-                out[i] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
-                                     G * (az[k].s - az[k].c), pot);
+                out[i - t0] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
+                                          G * (az[k].s - az[k].c), pot);
             }
         }
         return;
@@ -285,7 +286,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int n_tiles, int S, flo
             a3 += peer[3 * NB + q];
         }
         int i = i0 + q;
-        if (i < n) out[i] = make_float4(G * a0, G * a1, G * a2, POT ? -G * a3 : 0.f);
+        if (i < t_end) out[i - t0] = make_float4(G * a0, G * a1, G * a2, POT ? -G * a3 : 0.f);
     }
     cluster.sync();
 }
@@ -410,7 +411,7 @@ pp_gravity_batched_kernel(const float4 *__restrict__ pos, const int4 *__restrict
 // by a wave-quantisation cost model over the measured occupancy.
 // ---------------------------------------------------------------------------
 
-using GravKernel = void (*)(const float4 *, int, int, int, float, float, float4 *);
+using GravKernel = void (*)(const float4 *, int, int, int, int, int, float, float, float4 *);
 
 template <int RP>
 static GravKernel pick_kernel(bool pot, bool guard, bool kahan) {
@@ -480,29 +481,29 @@ static double plan_cost(long long units, int slots, int R, int n, int S) {
 
 static std::atomic<int> g_force_R{0}, g_force_S{0};
 
-static GravPlan plan_gravity_uncached(int n, bool pot, bool guard, bool kahan);
+static GravPlan plan_gravity_uncached(int m, int n, bool pot, bool guard, bool kahan);
 
-// Plans are cached per (n, variant) so that repeated launches (and launches
-// recorded into a CUDA graph) make no occupancy queries.
+// Plans are cached per (targets m, sources n, variant) so that repeated
+// launches (and launches recorded into a CUDA graph) make no occupancy queries.
 static std::mutex g_plan_mutex;
-static std::map<std::tuple<int, int>, GravPlan> g_plan_cache;
+static std::map<std::tuple<int, int, int>, GravPlan> g_plan_cache;
 
-static GravPlan plan_gravity(int n, bool pot, bool guard, bool kahan) {
+static GravPlan plan_gravity(int m, int n, bool pot, bool guard, bool kahan) {
     const int fR = g_force_R.load(), fS = g_force_S.load();
     if (fR) {
         const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
         return GravPlan{fR, std::max(1, std::min(fS, std::max(1, n_tiles)))};
     }
-    const auto key = std::make_tuple(n, (pot ? 1 : 0) | (guard ? 2 : 0) | (kahan ? 4 : 0));
+    const auto key = std::make_tuple(m, n, (pot ? 1 : 0) | (guard ? 2 : 0) | (kahan ? 4 : 0));
     std::lock_guard<std::mutex> lock(g_plan_mutex);
     auto it = g_plan_cache.find(key);
     if (it != g_plan_cache.end()) return it->second;
-    GravPlan p = plan_gravity_uncached(n, pot, guard, kahan);
+    GravPlan p = plan_gravity_uncached(m, n, pot, guard, kahan);
     g_plan_cache[key] = p;
     return p;
 }
 
-static GravPlan plan_gravity_uncached(int n, bool pot, bool guard, bool kahan) {
+static GravPlan plan_gravity_uncached(int m, int n, bool pot, bool guard, bool kahan) {
     const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
     GravPlan best{4, 1};
     double best_cost = 1e300;
@@ -510,7 +511,7 @@ static GravPlan plan_gravity_uncached(int n, bool pot, bool guard, bool kahan) {
     const int Ss[5] = {1, 2, 4, 8, 16};
     for (int R : Rs) {
         GravKernel k = kernel_for(R, pot, guard, kahan);
-        const long long nib = (n + GR_THREADS * R - 1) / (GR_THREADS * R);
+        const long long nib = (m + GR_THREADS * R - 1) / (GR_THREADS * R);
         for (int S : Ss) {
             if (S > 1 && S > n_tiles) break;
             int slots = slots_for(k, S);
@@ -639,24 +640,22 @@ int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *unit
 
 using namespace sphgb;
 
-extern "C" int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
-                          int32_t flags, sph_stream_t stream) {
-    if (n < 0 || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
-    if (n == 0) return SPH_OK;
-    if (!d_pos_m || !d_acc_pot) return SPH_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(d_pos_m) & 15u) || (reinterpret_cast<uintptr_t>(d_acc_pot) & 15u))
-        return SPH_ERR_INVALID_ARG;
+namespace {
+
+// One launch of the one-sided kernel over the targets [i0, i1) of n sources.
+int gravity_rows(const float *d_pos_m, int n, int i0, int i1, float G, float eps, float *d_acc_pot,
+                 int flags, sph_stream_t stream) {
     std::call_once(g_grav_once, grav_init);
     if (g_grav_init_status != SPH_OK) return g_grav_init_status;
-
+    const int m = i1 - i0;
     const bool pot = flags & SPH_GRAV_POTENTIAL;
     const bool kahan = !(flags & SPH_GRAV_NO_KAHAN);
     const float eps2 = eps * eps;
     const bool guard = !(eps2 > 0.0f);
-    GravPlan p = plan_gravity(n, pot, guard, kahan);
+    GravPlan p = plan_gravity(m, n, pot, guard, kahan);
     GravKernel k = kernel_for(p.R, pot, guard, kahan);
     const int n_tiles = (n + GR_TJ - 1) / GR_TJ;
-    const int nib = (n + GR_THREADS * p.R - 1) / (GR_THREADS * p.R);
+    const int nib = (m + GR_THREADS * p.R - 1) / (GR_THREADS * p.R);
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nib * p.S), 1, 1);
@@ -670,10 +669,33 @@ extern "C" int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, f
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = p.S > 1 ? 1 : 0;
-    SPH_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, reinterpret_cast<const float4 *>(d_pos_m), (int)n,
-                                    n_tiles, p.S, G, eps2, reinterpret_cast<float4 *>(d_acc_pot)));
+    SPH_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, reinterpret_cast<const float4 *>(d_pos_m), (int)n, i0,
+                                    i1, n_tiles, p.S, G, eps2, reinterpret_cast<float4 *>(d_acc_pot)));
     note_launch();
     return SPH_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" int pp_gravity(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
+                          int32_t flags, sph_stream_t stream) {
+    if (n < 0 || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
+    if (n == 0) return SPH_OK;
+    if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot))
+        return SPH_ERR_INVALID_ARG;
+    return gravity_rows(d_pos_m, n, 0, n, G, eps, d_acc_pot, flags, stream);
+}
+
+extern "C" int pp_gravity_rows(const float *d_pos_m, int32_t n, int32_t i0, int32_t i1, float G,
+                               float eps, float *d_acc_pot, int32_t flags, sph_stream_t stream) {
+    if (n < 0 || i0 < 0 || i1 < i0 || i1 > n || !(eps >= 0.0f) || !(G == G))
+        return SPH_ERR_INVALID_ARG;
+    if (i1 == i0) return SPH_OK;
+    if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot))
+        return SPH_ERR_INVALID_ARG;
+    return gravity_rows(d_pos_m, n, i0, i1, G, eps, d_acc_pot, flags, stream);
 }
 
 extern "C" int pp_gravity_status(sph_stream_t stream, int32_t *h_flags) {
@@ -724,7 +746,7 @@ extern "C" int sph_gravity_plan(int32_t n, int32_t flags, int32_t *h_R, int32_t 
     if (n <= 0 || !h_R || !h_S) return SPH_ERR_INVALID_ARG;
     std::call_once(g_grav_once, grav_init);
     if (g_grav_init_status != SPH_OK) return g_grav_init_status;
-    GravPlan p = plan_gravity(n, flags & SPH_GRAV_POTENTIAL, false, !(flags & SPH_GRAV_NO_KAHAN));
+    GravPlan p = plan_gravity(n, n, flags & SPH_GRAV_POTENTIAL, false, !(flags & SPH_GRAV_NO_KAHAN));
     *h_R = p.R;
     *h_S = p.S;
     return SPH_OK;

@@ -126,6 +126,7 @@ def lib():
             "sph_cfl_dt": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P]),
             "pp_gravity": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "pp_gravity_status": (_I, [_P, ctypes.POINTER(_I)]),
+            "pp_gravity_rows": (_I, [_P, _I, _I, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P]),
             "sph_set_wait_limit_ns": (_I, [_I64]),
             "sph_wait_probe": (_I, [_P]),
             "pp_gravity_pairs": (_I, [_P, _I, ctypes.c_float, ctypes.c_float, _P, _I, _P,
@@ -353,6 +354,15 @@ def pp_gravity(pos_m, acc_pot, G=1.0, eps=0.01, flags=0, stream=None):
                           _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"), int(flags),
                           _stream(stream))
     _check("pp_gravity", rc)
+
+
+def pp_gravity_rows(pos_m, i0, i1, acc_pot, G=1.0, eps=0.01, flags=0, stream=None):
+    """Gravity of the targets [i0, i1) over all sources of pos_m [n, 4] into
+    acc_pot [i1 - i0, 4]."""
+    n = pos_m.shape[0]
+    _check("pp_gravity_rows", lib().pp_gravity_rows(
+        _ptr(pos_m, torch.float32, (n, 4), "pos_m"), n, int(i0), int(i1), float(G), float(eps),
+        _ptr(acc_pot, torch.float32, (int(i1) - int(i0), 4), "acc_pot"), int(flags), _stream(stream)))
 
 
 def pp_gravity_pairs_workspace_bytes(n):

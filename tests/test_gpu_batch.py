@@ -101,3 +101,82 @@ def test_graph_replay_equals_step():
     torch.cuda.synchronize()
     assert np.array_equal(a.positions(), b.positions())
     assert np.array_equal(a.velocities(), b.velocities())
+
+
+def test_batched_sph_stages_match_the_oracle_per_simulation(orc):
+    # Four gas-carrying simulations laid on top of one another (every halo is
+    # centred on the origin, so their particles interleave in space and in the
+    # shared hashed grid): the batch's sort, neighbour search, density and
+    # forces, run as one launch per stage, against the oracle on each
+    # simulation alone -- neighbour sets exact (no pair crosses simulations),
+    # density and the hydro right-hand side within the stated tolerances.
+    torch = need_gpu()
+    from helpers import RMS_TOL, MAX_TOL, max_plain, pos_h_of
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.sim import assemble_batch
+    lst = [ics.two_halo(1500, 500, seed=61), ics.single_halo(2500, 700, seed=62),
+           ics.single_halo(900, 0, seed=63), ics.two_halo(350, 350, seed=64)]
+    rng = np.random.default_rng(65)
+    for d in lst:   # stir the gas so viscosity and heating act
+        d["v"] = d["v"].copy()
+        d["v"][:d["n_gas"]] = rng.normal(scale=0.3, size=(d["n_gas"], 3))
+    ic, go, do, so = assemble_batch(lst)
+    ng = int(ic["n_gas"])
+    ph = pos_h_of(ic["r"][:ng], ic["h"])
+    mass = ic["m"][:ng].astype(np.float32)
+    ve = np.empty((ng, 4), np.float32)
+    ve[:, :3] = ic["v"][:ng]
+    ve[:, 3] = ic["e"]
+    cu = lambda a: torch.as_tensor(a, device="cuda")
+    batch = nv.Batch(go, do, cu(so))
+    ctx = nv.Ctx(ng, 250 * ng)
+    nv.sph_ctx_set_batch(ctx, batch)
+    perm = torch.empty(ng, dtype=torch.int32, device="cuda")
+    nv.sph_bin_and_sort(ctx, cu(ph), perm=perm)
+    start = torch.empty(ng + 1, dtype=torch.int32, device="cuda")
+    need = nv.sph_build_neighbors(ctx, ng, nb_start=start)
+    idx = torch.empty(max(need, 1), dtype=torch.int32, device="cuda")
+    nv.sph_build_neighbors(ctx, ng, nb_start=start, nb_idx=idx)
+    rho = torch.empty(ng, device="cuda")
+    hn = torch.empty(ng, device="cuda")
+    nv.sph_density(ctx, cu(mass), rho, hn)
+    torch.cuda.synchronize()
+    rho_g = rho.cpu().numpy()
+    # forces from a common density input: the oracle's, per simulation
+    rho_in = np.empty(ng, np.float32)
+    for s in range(len(lst)):
+        a, b = go[s], go[s + 1]
+        if b > a:
+            rho_in[a:b], _ = orc.density(ph[a:b], mass[a:b])
+    acc = torch.full((ng, 4), float("nan"), device="cuda")
+    nv.sph_forces(ctx, cu(ve), cu(rho_in), cu(mass), acc)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    acc_g = acc.cpu().numpy().astype(np.float64)
+    perm = perm.cpu().numpy()
+    start = start.cpu().numpy()
+    idx = idx.cpu().numpy()[:need]
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(ng, dtype=perm.dtype)
+    for s in range(len(lst)):
+        a, b = int(go[s]), int(go[s + 1])
+        if b == a:
+            continue
+        # neighbour sets of every row of this simulation, against brute force
+        # over this simulation's gas alone
+        ost, oidx = orc.neighbors(ph[a:b])
+        for i in range(a, b):
+            k = inv[i]
+            got = np.sort(perm[idx[start[k]:start[k + 1]]])
+            ref = np.sort(oidx[ost[i - a]:ost[i - a + 1]] + a)
+            assert np.array_equal(got, ref), (s, i)
+        orho, _ = orc.density(ph[a:b], mass[a:b])
+        r1, m1 = err(rho_g[a:b], orho)
+        assert r1 <= 1e-6 and m1 <= 1e-5, (s, r1, m1)
+        oa, ode = orc.hydro(ph[a:b], ve[a:b], mass[a:b], rho_in[a:b])
+        ra, ma = err(acc_g[a:b, :3], oa)
+        re_, me = err(acc_g[a:b, 3:], ode[:, None])
+        print(f"batch sim {s} ({b - a} gas): rho rms {r1:.1e}; accel rms {ra:.1e} max {ma:.1e} "
+              f"(plain {max_plain(acc_g[a:b, :3], oa):.1e}); de/dt rms {re_:.1e} max {me:.1e}")
+        assert ra <= RMS_TOL and ma <= MAX_TOL, (s, ra, ma)
+        assert re_ <= RMS_TOL and me <= MAX_TOL, (s, re_, me)
