@@ -668,6 +668,68 @@ def run_serve(args):
     return 0
 
 
+def run_gravity_sharded(args):
+    """Gravity over --n particles split across the ranks by the paper's
+    particle partition (Sect. 3): per launch, one all-gather of (x, y, z, m)
+    (NCCL) and each rank's own rows over all sources (pp_gravity_rows, the
+    one-sided kernel).  Total work is fixed (strong scaling); value = N^2
+    interactions / the slowest rank's time per launch."""
+    import torch
+
+    from paper_1807_08116_gb300 import ics
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.shard import owned_rows, sharded_gravity
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    nv.lib()
+    q = args.n // 4
+    d = ics.two_halo(q, q, seed=2)      # the same particles on every rank
+    n = d["n"]
+    i0, i1 = owned_rows(n)
+    pm = np.empty((n, 4), np.float32)
+    pm[:, :3] = d["r"]
+    pm[:, 3] = d["m"]
+    x = torch.as_tensor(pm[i0:i1].copy(), device="cuda")
+    out = torch.empty((i1 - i0, 4), device="cuda")
+
+    def launch():
+        sharded_gravity(x, n, out)
+    for _ in range(args.warmup):
+        launch()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    if nv.pp_gravity_status():
+        raise RuntimeError("gravity kernel reported a timeout")
+    ips = float(n) * n / (ms / 1e3)
+    if rank == 0:
+        print(json.dumps({"metric": "PP interactions/s", "value": ips, "unit": "interactions/s",
+                          "n": n, "n_gpus": world, "ms_per_launch": ms, "steps": args.steps,
+                          "warmup": args.warmup, "scaling": "strong",
+                          "config": {"workload": f"gravity of the two-halo construction, {n} bodies",
+                                     "parallelism": f"particle partition over {world} rank(s): "
+                                                    "all-gather of (x, y, z, m), own rows"},
+                          "kernel": "pp_gravity_kernel (rows)",
+                          "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_gravity(args):
     """Gravity kernel alone on the two-halo construction with --n particles
     (the same inputs the step uses): --warmup untimed and --steps timed
@@ -677,6 +739,8 @@ def run_gravity(args):
     from paper_1807_08116_gb300 import ics
     from paper_1807_08116_gb300 import native as nv
 
+    if args.shard:
+        return run_gravity_sharded(args)
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     nv.lib()
     q = args.n // 4
@@ -736,6 +800,9 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity")
     ap.add_argument("--one-sided", action="store_true",
                     help="--workload gravity: time the one-sided kernel instead of the pair-once one")
+    ap.add_argument("--shard", action="store_true",
+                    help="--workload gravity: split the rows over the ranks (particle partition, "
+                         "one all-gather of the sources per launch)")
     ap.add_argument("--n-sims", type=int, default=64)
     ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--serve-window", type=float, default=90.0)
