@@ -168,7 +168,7 @@ __device__ __forceinline__ void fold_tile(Kahan (&ax)[2 * RP], Kahan (&ay)[2 * R
 // straight from two broadcast 16-byte shared loads.
 template <int RP, bool POT, bool GUARD, bool KAHAN>
 __global__ void __launch_bounds__(GR_THREADS, RP >= 4 ? 1 : SPHGB_GR_MINB)
-pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int n_tiles, int S,
+pp_gravity_kernel(const float4 *__restrict__ pos, int n, int row0, int row_end, int n_tiles, int S,
                   float G, float eps2, float4 *__restrict__ out) {
     constexpr int R = 2 * RP;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -177,8 +177,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int 
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + GR_SMEM - 64);
     const int tid = threadIdx.x;
     const int rank = blockIdx.x % S;   // cluster dims (S, 1, 1): rank == ctarank
-    // targets [t0, t_end) of the n sources; target i is written to out[i - t0]
-    const int i0 = t0 + (blockIdx.x / S) * (GR_THREADS * R);
+    // targets [row0, row_end) of the n sources; target i is written to out[i - row0]
+    const int i0 = row0 + (blockIdx.x / S) * (GR_THREADS * R);
     const int t_begin = (int)((long long)n_tiles * rank / S);
     const int t_end = (int)((long long)n_tiles * (rank + 1) / S);
     const int my_tiles = t_end - t_begin;
@@ -189,8 +189,8 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int 
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
         int ia = i0 + tid + (2 * p) * GR_THREADS, ib = ia + GR_THREADS;
-        float4 a = ia < t_end ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 b = ib < t_end ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 a = ia < row_end ? pos[ia] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 b = ib < row_end ? pos[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
         nx[p] = make_float2(-a.x, -b.x);
         ny[p] = make_float2(-a.y, -b.y);
         nz[p] = make_float2(-a.z, -b.z);
@@ -251,9 +251,9 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             int i = i0 + tid + k * GR_THREADS;
-            if (i < t_end) {
+            if (i < row_end) {
                 float pot = POT ? -G * (ph[k].s - ph[k].c) : 0.f;
-                out[i - t0] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
+                out[i - row0] = make_float4(G * (ax[k].s - ax[k].c), G * (ay[k].s - ay[k].c),
                                           G * (az[k].s - az[k].c), pot);
             }
         }
@@ -286,7 +286,7 @@ pp_gravity_kernel(const float4 *__restrict__ pos, int n, int t0, int t_end, int 
             a3 += peer[3 * NB + q];
         }
         int i = i0 + q;
-        if (i < t_end) out[i - t0] = make_float4(G * a0, G * a1, G * a2, POT ? -G * a3 : 0.f);
+        if (i < row_end) out[i - row0] = make_float4(G * a0, G * a1, G * a2, POT ? -G * a3 : 0.f);
     }
     cluster.sync();
 }
