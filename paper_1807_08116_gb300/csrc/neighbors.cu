@@ -52,14 +52,17 @@ __device__ __forceinline__ void search_box(float x, float R, float x0, float inv
     hi = cell_of(__fadd_rn(x, m), x0, inv_c);
 }
 
-// Distance from coordinate x to cell c of size csz (origin x0), less a
-// rounding margin m; the end cells also hold everything clamped into them,
-// so they are open on their outer side.
-__device__ __forceinline__ float cell_gap(float x, int c, float csz, float x0, float m) {
-    const float lo = fmaf((float)c, csz, x0);
-    const float below = c > 0 ? lo - x : -1.0f;
-    const float above = c < kCellMax ? x - (lo + csz) : -1.0f;
-    return fmaxf(0.0f, fmaxf(below, above) - m);
+// Distance, in cell units, from a row at u = (x - x0) / csz to cell c,
+// less the rounding margin m (cell units); uh = u - 1/2.
+// The end cells also hold everything clamped into them, so they are open on
+// their outer side (EDGE: the box may touch them).  The margin m covers the
+// rounding of u, of this expression and of the neighbour predicate: the cut
+// never drops a cell that holds a row's neighbour (see search_box).
+template <bool EDGE>
+__device__ __forceinline__ float cell_gap_u(float uh, int c, float m_half) {
+    float d = fmaxf(fabsf(uh - (float)c) - m_half, 0.0f);   // m_half = 1/2 + m
+    if (EDGE && ((c == 0 && uh < 0.0f) || (c == kCellMax && uh > (float)kCellMax))) d = 0.0f;
+    return d;
 }
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -67,6 +70,13 @@ constexpr int kNbWarps = 4;   // warps (row groups of 32) per block
 // rows whose cell lies within this many cells of the leader's join its group
 // (2, 3 and 4 measured; 3 and 4 within 1% of each other, 2 is 10% slower)
 constexpr int kNbGroupReach = 3;
+// The first own entries of each row are staged in shared memory, column by
+// column (entry c of the warp's lane r at c * 33 + r: conflict-free when the
+// lanes append their c-th entries together, and when one row is read back by
+// the whole warp), and written to the global staging rows with coalesced
+// stores once the warp is done; later entries go to global memory directly.
+constexpr int kStageSmem = 44;
+constexpr int kStageStride = 33;
 
 // MODE: NB_COUNT counts own entries (and reverse entries of the coarser
 // partners); NB_FILL writes own and reverse entries into their CSR places;
@@ -80,7 +90,7 @@ enum { NB_COUNT = 0, NB_FILL = 1, NB_STAGE = 2, NB_FILL_LISTED = 3 };
 // (i in the row of j) when j sits on a coarser level.
 template <int MODE>
 __device__ __forceinline__ void nb_accept(const NbArgs &a, int i, int j, bool coarser,
-                                          long long base, int &cnt) {
+                                          long long base, int &cnt, int *sstage, int lane) {
     constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
     if (FILL) {
         const long long w = base + cnt;
@@ -93,9 +103,12 @@ __device__ __forceinline__ void nb_accept(const NbArgs &a, int i, int j, bool co
             else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
         }
     } else {
-        // the top bit marks a coarser partner for the copy pass
-        if (MODE == NB_STAGE && cnt < a.stage_k)
-            a.stage[(long long)i * a.stage_k + cnt] = coarser ? (int)((unsigned)j | 0x80000000u) : j;
+        if (MODE == NB_STAGE) {
+            // the top bit marks a coarser partner for the copy pass
+            const int v = coarser ? (int)((unsigned)j | 0x80000000u) : j;
+            if (cnt < kStageSmem) sstage[cnt * kStageStride + lane] = v;
+            else if (cnt < a.stage_k) a.stage[(long long)i * a.stage_k + cnt] = v;
+        }
         if (coarser) atomicAdd(&a.rev[j], 1);
     }
     ++cnt;
@@ -104,12 +117,17 @@ __device__ __forceinline__ void nb_accept(const NbArgs &a, int i, int j, bool co
 template <int MODE>
 __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
     constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
-    __shared__ float4 s_q[kNbWarps][32];
+    // candidates of a batch as columns, so pairs of them feed packed FP32x2
+    // operations from 8-byte loads
+    __shared__ __align__(16) float s_cx[kNbWarps][32], s_cy[kNbWarps][32], s_cz[kNbWarps][32],
+        s_ch[kNbWarps][32];
     __shared__ int s_j[kNbWarps][32];
-    const int lane = threadIdx.x & 31;
-    float4 *sq = s_q[threadIdx.x >> 5];
-    int *sj = s_j[threadIdx.x >> 5];
-    const long long r = ((long long)blockIdx.x * kNbWarps + (threadIdx.x >> 5)) * 32 + lane;
+    __shared__ int s_stage[MODE == NB_STAGE ? kNbWarps : 1][MODE == NB_STAGE ? kStageSmem * kStageStride : 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *sqx = s_cx[wib], *sqy = s_cy[wib], *sqz = s_cz[wib], *sqh = s_ch[wib];
+    int *sj = s_j[wib];
+    int *sstage = s_stage[MODE == NB_STAGE ? wib : 0];
+    const long long r = ((long long)blockIdx.x * kNbWarps + wib) * 32 + lane;
     const int rows = MODE == NB_FILL_LISTED ? *a.list_count : a.n;
     const bool act = r < rows;
     unsigned todo = __ballot_sync(kFull, act);
@@ -122,6 +140,8 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
     int cnt = 0;
     long long base = 0;
     if (FILL && act) base = a.nb_start[i];
+    const float2 px2 = make_float2(p.x, p.x), py2 = make_float2(p.y, p.y),
+                 pz2 = make_float2(p.z, p.z);
     while (todo) {
         // the next group: the lowest pending row and the pending rows of its
         // simulation and level whose cells are near the leader's
@@ -171,10 +191,16 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                 solo = (long long)(ux + 1) * (uy + 1) * (uz + 1) > (1ll << 24);
             }
             const float csz = pow2f(g.log2_L0 + l);
-            // |coordinate| of anything in the row's box is at most |x0| + (hi + 1) csz
-            const float mx = 9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f;
-            const float my = 9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f;
-            const float mz = 9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f;
+            // the row in cell units of this level, less half a cell, and its
+            // rounding margins (|coordinate| of anything in the row's box is
+            // at most |x0| + (hi + 1) csz; 2^-20 of that covers the rounding of
+            // the predicate, of the cell binning and of the distance below)
+            const float uhx = __fmul_rn(__fsub_rn(p.x, g.x0), inv_c) - 0.5f;
+            const float uhy = __fmul_rn(__fsub_rn(p.y, g.y0), inv_c) - 0.5f;
+            const float uhz = __fmul_rn(__fsub_rn(p.z, g.z0), inv_c) - 0.5f;
+            const float mhx = 0.5f + (9.5367431640625e-07f * (fabsf(p.x) + 2.0f * fabsf(g.x0) + (float)(hx + 2) * csz) + 1e-30f) * inv_c;
+            const float mhy = 0.5f + (9.5367431640625e-07f * (fabsf(p.y) + 2.0f * fabsf(g.y0) + (float)(hy + 2) * csz) + 1e-30f) * inv_c;
+            const float mhz = 0.5f + (9.5367431640625e-07f * (fabsf(p.z) + 2.0f * fabsf(g.z0) + (float)(hz + 2) * csz) + 1e-30f) * inv_c;
             const unsigned salt = ((unsigned)l + salt_sim) * (unsigned)kLevelSalt;
             const unsigned kmask = (1u << g.log2_M) - 1u;
             while (pend) {
@@ -200,12 +226,18 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                             }
                     if (!any) continue;
                 }
+                // the end cells are open on their outer side: only boxes that
+                // touch them take the slower distance
+                const bool edge = LX == 0 || LY == 0 || LZ == 0 || HX == kCellMax || HY == kCellMax ||
+                                  HZ == kCellMax;
                 // The union box is walked 32 cells at a time in z, y, x order:
                 // lane t probes cell c0 + t, so the bucket reads of 32 cells
                 // are one round trip.  A row's predicate sees only its own
                 // level's candidates (its h is replaced by NaN, which fails
                 // every test, when it takes no part in this level).
-                const float4 pr = make_float4(p.x, p.y, p.z, in ? p.w : __uint_as_float(0x7fc00000u));
+                const float2 ph2 = in ? make_float2(p.w, p.w) : make_float2(__uint_as_float(0x7fc00000u),
+                                                                           __uint_as_float(0x7fc00000u));
+                const float ihw = in ? __fmul_rn(p.w, inv_c) : 0.0f;
                 const int NX = HX - LX + 1, NY = HY - LY + 1;
                 const int ncell = NX * NY * (HZ - LZ + 1);
                 for (int c0 = 0; c0 < ncell; c0 += 32) {
@@ -222,20 +254,29 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         e = a.cell_start[k + 1];
                         hm = a.hmax_cell[k];
                     }
-                    unsigned live = __ballot_sync(kFull, s < e);
+                    const unsigned live = __ballot_sync(kFull, s < e);
                     if (live == 0u) continue;
+                    // the bucket's max h in cell units, by the lane that read it
+                    const float hmc = __fmul_rn(__uint_as_float(hm), inv_c);
                     // keep the cells some row of the group can reach: within
-                    // h_i + hmax of the bucket, widened by the binning's
-                    // rounding margin (a conservative cut, as the box is)
+                    // h_i + hmax of the bucket, widened by the rounding margins
+                    // (a conservative cut, as the box is)
                     unsigned want = 0u;
                     for (unsigned lv = live; lv; lv &= lv - 1u) {
                         const int t = __ffs(lv) - 1;
                         const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
                                   cz = __shfl_sync(kFull, tz, t);
-                        const float reach = p.w + __uint_as_float(__shfl_sync(kFull, hm, t));
-                        const float dx = cell_gap(p.x, cx, csz, g.x0, mx);
-                        const float dy = cell_gap(p.y, cy, csz, g.y0, my);
-                        const float dz = cell_gap(p.z, cz, csz, g.z0, mz);
+                        const float reach = ihw + __shfl_sync(kFull, hmc, t);
+                        float dx, dy, dz;
+                        if (edge) {
+                            dx = cell_gap_u<true>(uhx, cx, mhx);
+                            dy = cell_gap_u<true>(uhy, cy, mhy);
+                            dz = cell_gap_u<true>(uhz, cz, mhz);
+                        } else {
+                            dx = cell_gap_u<false>(uhx, cx, mhx);
+                            dy = cell_gap_u<false>(uhy, cy, mhy);
+                            dz = cell_gap_u<false>(uhz, cz, mhz);
+                        }
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         const bool need = in && !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
                         if (__ballot_sync(kFull, need)) want |= 1u << t;
@@ -278,25 +319,64 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         __syncwarp();   // the previous batch has been read
                         if (ok) {
                             const int slot = __popc(okm & ((1u << lane) - 1u));
-                            sq[slot] = q;
+                            sqx[slot] = q.x;
+                            sqy[slot] = q.y;
+                            sqz[slot] = q.z;
+                            sqh[slot] = q.w;
                             sj[slot] = jl;
                         }
+                        if ((nok & 1) && lane == 0) {
+                            // an odd batch gets a padding column that fails
+                            // every test (h = NaN)
+                            sqx[nok] = 0.0f;
+                            sqy[nok] = 0.0f;
+                            sqz[nok] = 0.0f;
+                            sqh[nok] = __uint_as_float(0x7fc00000u);
+                        }
                         __syncwarp();
-                        // the predicate over the batch first, collecting a
-                        // bit per accepted candidate; then the appends, in
-                        // candidate order, with no branch per candidate
+                        // the predicate over the batch first, two candidates
+                        // per packed FP32x2 operation (each element rounded
+                        // as the scalar form is), collecting a bit per
+                        // accepted candidate; then the appends, in candidate
+                        // order, with no branch per candidate
                         unsigned acc = 0u;
-                        for (int u = 0; u < nok; ++u)
-                            if (nb_pred(pr, sq[u])) acc |= 1u << u;
+                        for (int u = 0; u < nok; u += 2) {
+                            const float2 qx2 = *reinterpret_cast<const float2 *>(sqx + u);
+                            const float2 qy2 = *reinterpret_cast<const float2 *>(sqy + u);
+                            const float2 qz2 = *reinterpret_cast<const float2 *>(sqz + u);
+                            const float2 qh2 = *reinterpret_cast<const float2 *>(sqh + u);
+                            const float2 dx = __fadd2_rn(px2, make_float2(-qx2.x, -qx2.y));
+                            const float2 dy = __fadd2_rn(py2, make_float2(-qy2.x, -qy2.y));
+                            const float2 dz = __fadd2_rn(pz2, make_float2(-qz2.x, -qz2.y));
+                            const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)),
+                                                         __fmul2_rn(dz, dz));
+                            const float2 sh = __fadd2_rn(ph2, qh2);
+                            const float2 s2 = __fmul2_rn(sh, sh);
+                            if (r2.x < s2.x) acc |= 1u << u;
+                            if (r2.y < s2.y) acc |= 2u << u;
+                        }
                         while (acc) {
                             const int u = __ffs(acc) - 1;
                             acc &= acc - 1u;
                             const int jt = sj[u];
-                            if (jt != i) nb_accept<MODE>(a, i, jt, l > lg, base, cnt);
+                            if (jt != i) nb_accept<MODE>(a, i, jt, l > lg, base, cnt, sstage, lane);
                         }
                     }
                 }
             }
+        }
+    }
+    if (MODE == NB_STAGE) {
+        // the staged entries of the warp's rows, row by row, as coalesced
+        // stores into the global staging rows
+        __syncwarp();
+        const int mine = act ? min(cnt, kStageSmem) : 0;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int cr = __shfl_sync(kFull, mine, rr);
+            const int ir = __shfl_sync(kFull, i, rr);
+            if (lane < cr) a.stage[(long long)ir * a.stage_k + lane] = sstage[lane * kStageStride + rr];
+            if (lane + 32 < cr)
+                a.stage[(long long)ir * a.stage_k + lane + 32] = sstage[(lane + 32) * kStageStride + rr];
         }
     }
     if (act) {
