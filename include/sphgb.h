@@ -101,6 +101,12 @@ int sph_ctx_destroy(sph_ctx *ctx);
  * order of the per-lane partial sums. */
 int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes);
 
+/* How sph_bin_and_sort runs the sorting stage: 1 (default) as one
+ * cooperative launch whose phases are separated by grid-wide barriers, 0 as
+ * a sequence of kernels (the form it also takes while `stream` is being
+ * captured into a CUDA graph).  Both give bitwise the same results. */
+int sph_ctx_set_sort_fused(sph_ctx *ctx, int32_t fused);
+
 /* Replace the model constants used by later calls. */
 int sph_ctx_set_params(sph_ctx *ctx, const SphParams *params);
 

@@ -74,6 +74,8 @@ struct sph_ctx {
     unsigned *lvl_hmax;
     GridDev *grid;
     unsigned *red;
+    unsigned *red_fused;   // extremes of the one-launch sort (0 between calls)
+    int block_sums_cap;
     int *flags;
     int *block_sums;
     float4 *pos_h_s, *vel_s, *aux_s;
@@ -84,6 +86,7 @@ struct sph_ctx {
     int nb_built;    // 1 once lists match the last sort
     int sorted_batched;        // the last sort used the batch's simulation map
     int hydro_lanes;           // lanes per row in DC / HFC (1, 2, 4 or 8)
+    int sort_fused;            // 1: the sorting stage as one cooperative launch
     const sph_batch *batch;    // NULL: one simulation
 };
 
@@ -135,9 +138,11 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->lvl_hmax = cv.take<unsigned>(kMaxLevels);
     c->grid = cv.take<GridDev>(1);
     c->red = cv.take<unsigned>(8);
+    c->red_fused = cv.take<unsigned>(8);
     c->flags = cv.take<int>(4);
     size_t nb_scan = (size_t)scan_block_count((long long)(M > n ? M : n));
     c->block_sums = cv.take<int>(nb_scan + 32);
+    c->block_sums_cap = (int)(nb_scan + 32);
     c->pos_h_s = cv.take<float4>(n);
     c->vel_s = cv.take<float4>(n);
     c->aux_s = cv.take<float4>(n);
@@ -201,6 +206,7 @@ extern "C" int sph_ctx_create(const SphParams *params, int32_t n_gas_max, int32_
     c->ws = d_workspace;
     c->ws_bytes = workspace_bytes;
     c->hydro_lanes = 4;
+    c->sort_fused = 1;
     size_t total = 0;
     carve(c, static_cast<char *>(d_workspace), &total);
     if (cudaMemsetAsync(d_workspace, 0, total, (cudaStream_t)stream) != cudaSuccess) {
@@ -219,6 +225,12 @@ extern "C" int sph_ctx_destroy(sph_ctx *ctx) {
 extern "C" int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes) {
     if (!ctx || (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)) return SPH_ERR_INVALID_ARG;
     ctx->hydro_lanes = lanes;
+    return SPH_OK;
+}
+
+extern "C" int sph_ctx_set_sort_fused(sph_ctx *ctx, int32_t fused) {
+    if (!ctx || (fused != 0 && fused != 1)) return SPH_ERR_INVALID_ARG;
+    ctx->sort_fused = fused;
     return SPH_OK;
 }
 
@@ -284,32 +296,71 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
     cudaStream_t st = (cudaStream_t)stream;
     const float4 *pos = reinterpret_cast<const float4 *>(d_pos_h);
     const int M = (int)ctx->M;
-    int rc;
-    if (h_grid) rc = launch_grid_set(*h_grid, ctx->grid, st);
-    else rc = launch_grid_auto(pos, n_gas, ctx->red, ctx->log2_M, ctx->grid, st);
-    if (rc) return rc;
-    // SP0: zero the per-bucket and per-level arrays
-    SPH_CUDA_TRY(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)M, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(ctx->hmax_cell, 0, sizeof(unsigned) * (size_t)M, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(ctx->occ, 0, sizeof(unsigned) * ((size_t)M / 16 + 1), st));
-    SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_count, 0, sizeof(int) * kMaxLevels, st));
-    SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
-    // SP1
     const int *sim_of = ctx->batch ? ctx->batch->d_sim_of_gas : nullptr;
     if (sim_of && n_gas != ctx->batch->n_gas) return SPH_ERR_INVALID_ARG;
-    if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->key, ctx->count, st))) return rc;
-    // SP2 + SP3
-    if ((rc = launch_scan_exclusive(ctx->count, M, ctx->start, ctx->block_sums, st))) return rc;
-    // SP4 + canonical order inside buckets
-    if ((rc = launch_scatter(ctx->key, n_gas, ctx->start, ctx->count, ctx->tmp, st))) return rc;
-    if ((rc = launch_sort_buckets(ctx->key, n_gas, ctx->start, ctx->tmp, ctx->perm, ctx->long_list,
-                                  ctx->long_count, st)))
-        return rc;
-    // sorted copies and the bucket / super-cell / level statistics
-    if ((rc = launch_gather_bin(pos, sim_of, ctx->perm, n_gas, ctx->grid, ctx->pos_h_s,
-                                sim_of ? ctx->sim_s : nullptr, ctx->occ, ctx->log2_M + 1,
-                                ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
-        return rc;
+    int rc;
+    // The whole stage as one cooperative launch; while the stream is being
+    // captured into a graph (or if the launch is refused) the same stage runs
+    // as the sequence of kernels below, with bitwise the same results.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SPH_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    bool fused = false;
+    if (cap == cudaStreamCaptureStatusNone && ctx->sort_fused) {
+        SortArgs fa{};
+        fa.pos_h = pos;
+        fa.sim_of = sim_of;
+        fa.n = n_gas;
+        fa.log2_M = ctx->log2_M;
+        fa.auto_grid = h_grid ? 0 : 1;
+        if (h_grid)
+            fa.given = GridDev{h_grid->x0, h_grid->y0, h_grid->z0, h_grid->log2_L0, h_grid->n_levels,
+                               h_grid->log2_M};
+        fa.red = ctx->red_fused;
+        fa.grid = ctx->grid;
+        fa.key = ctx->key;
+        fa.count = ctx->count;
+        fa.start = ctx->start;
+        fa.block_sums = ctx->block_sums;
+        fa.block_sums_cap = ctx->block_sums_cap;
+        fa.tmp = ctx->tmp;
+        fa.perm = ctx->perm;
+        fa.long_list = ctx->long_list;
+        fa.long_count = ctx->long_count;
+        fa.pos_h_s = ctx->pos_h_s;
+        fa.sim_s = sim_of ? ctx->sim_s : nullptr;
+        fa.occ = ctx->occ;
+        fa.log2_B = ctx->log2_M + 1;
+        fa.hmax_cell = ctx->hmax_cell;
+        fa.lvl_count = ctx->lvl_count;
+        fa.lvl_hmax = ctx->lvl_hmax;
+        if (launch_sort_fused(fa, st) == SPH_OK) fused = true;
+        else cudaGetLastError();   // a refused launch leaves no sticky error
+    }
+    if (!fused) {
+        if (h_grid) rc = launch_grid_set(*h_grid, ctx->grid, st);
+        else rc = launch_grid_auto(pos, n_gas, ctx->red, ctx->log2_M, ctx->grid, st);
+        if (rc) return rc;
+        // SP0: zero the per-bucket and per-level arrays
+        SPH_CUDA_TRY(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)M, st));
+        SPH_CUDA_TRY(cudaMemsetAsync(ctx->hmax_cell, 0, sizeof(unsigned) * (size_t)M, st));
+        SPH_CUDA_TRY(cudaMemsetAsync(ctx->occ, 0, sizeof(unsigned) * ((size_t)M / 16 + 1), st));
+        SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_count, 0, sizeof(int) * kMaxLevels, st));
+        SPH_CUDA_TRY(cudaMemsetAsync(ctx->lvl_hmax, 0, sizeof(unsigned) * kMaxLevels, st));
+        // SP1
+        if ((rc = launch_bin(pos, sim_of, n_gas, ctx->grid, ctx->key, ctx->count, st))) return rc;
+        // SP2 + SP3
+        if ((rc = launch_scan_exclusive(ctx->count, M, ctx->start, ctx->block_sums, st))) return rc;
+        // SP4 + canonical order inside buckets
+        if ((rc = launch_scatter(ctx->key, n_gas, ctx->start, ctx->count, ctx->tmp, st))) return rc;
+        if ((rc = launch_sort_buckets(ctx->key, n_gas, ctx->start, ctx->tmp, ctx->perm, ctx->long_list,
+                                      ctx->long_count, st)))
+            return rc;
+        // sorted copies and the bucket / super-cell / level statistics
+        if ((rc = launch_gather_bin(pos, sim_of, ctx->perm, n_gas, ctx->grid, ctx->pos_h_s,
+                                    sim_of ? ctx->sim_s : nullptr, ctx->occ, ctx->log2_M + 1,
+                                    ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
+            return rc;
+    }
     ctx->sorted_batched = sim_of != nullptr;
     ctx->n_sorted = n_gas;
     ctx->nb_built = 0;

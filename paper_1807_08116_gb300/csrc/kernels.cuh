@@ -25,6 +25,29 @@ int launch_gather_bin(const float4 *pos_h, const int *sim_of, const int *perm, i
                       const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *occ, int log2_B,
                       unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st);
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
+// the whole sorting stage (grid, bin, scan, scatter, rank, long buckets,
+// sorted copies and statistics) as one cooperative launch; bitwise the
+// results of the launches above in sequence
+struct SortArgs {
+    const float4 *pos_h;
+    const int *sim_of;      // simulation of each particle, or NULL
+    int n;
+    int log2_M;
+    int auto_grid;          // 1: derive the grid; 0: use `given`
+    GridDev given;
+    unsigned *red;          // [5] extremes, 0 between calls
+    GridDev *grid;          // out
+    int *key, *count, *start, *block_sums, *tmp, *perm, *long_list, *long_count;
+    int block_sums_cap;     // entries of block_sums (bounds the grid)
+    float4 *pos_h_s;
+    int *sim_s;             // or NULL
+    unsigned *occ;
+    int log2_B;
+    unsigned *hmax_cell;
+    int *lvl_count;
+    unsigned *lvl_hmax;
+};
+int launch_sort_fused(const SortArgs &a, cudaStream_t st);
 void grid_reset_red(unsigned *red, const unsigned *v, cudaStream_t st);
 
 // gravity.cu: the batched kernel's work description (host side)

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -75,8 +77,9 @@ __device__ __forceinline__ int ceil_log2_pos(float v) {
     return mant ? fl + 1 : fl;
 }
 
-__global__ void grid_finalize_kernel(const unsigned *red, int log2_M, GridDev *grid) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The grid from the reduced extremes: red[0..3] ordered-min of x, y, z, h
+// (0xffffffff: none), red[4] ordered-max of h (0: none).
+__device__ __forceinline__ GridDev grid_from_red(const unsigned red[5], int log2_M) {
     float mins[3];
     for (int d = 0; d < 3; ++d) {
         float v = red[d] == 0xffffffffu ? 0.0f : ordered_to_float(red[d]);
@@ -89,12 +92,20 @@ __global__ void grid_finalize_kernel(const unsigned *red, int log2_M, GridDev *g
     int top = ceil_log2_pos(hmax) - l0;   // levels above L0 needed for hmax
     int nl = 1 + max(0, top);
     nl = min(nl, 24);
-    grid->x0 = mins[0];
-    grid->y0 = mins[1];
-    grid->z0 = mins[2];
-    grid->log2_L0 = l0;
-    grid->n_levels = nl;
-    grid->log2_M = log2_M;
+    GridDev g;
+    g.x0 = mins[0];
+    g.y0 = mins[1];
+    g.z0 = mins[2];
+    g.log2_L0 = l0;
+    g.n_levels = nl;
+    g.log2_M = log2_M;
+    return g;
+}
+
+__global__ void grid_finalize_kernel(const unsigned *red, int log2_M, GridDev *grid) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned r[5] = {red[0], red[1], red[2], red[3], red[4]};
+    *grid = grid_from_red(r, log2_M);
 }
 
 __global__ void grid_set_kernel(GridDev g, GridDev *grid) {
@@ -409,8 +420,48 @@ __device__ __forceinline__ int co_rank(int k, const int *A, int na, const int *B
     return lo;
 }
 
-// The sorted segment is left in out, which may be data itself or the
-// scratch array tmp (the three may alias, hence no __restrict__).
+// Sort segment [b, e) of data with the whole block (sm: SEG_CHUNK ints of
+// shared memory).  The sorted segment is left in out, which may be data
+// itself or the scratch array tmp (the three may alias, hence no
+// __restrict__).
+__device__ void segsort_one(int b, int e, int *data, int *tmp, int *out, int *sm) {
+    const int len = e - b;
+    if (len <= SEG_CHUNK) {
+        chunk_sort(data, b, len, sm);
+        if (out != data) {
+            for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = data[b + q];
+            __syncthreads();
+        }
+        return;
+    }
+    for (int c0 = 0; c0 < len; c0 += SEG_CHUNK) chunk_sort(data, b + c0, min(SEG_CHUNK, len - c0), sm);
+    int *src = data, *dst = tmp;
+    for (int width = SEG_CHUNK; width < len; width *= 2) {
+        for (int p0 = 0; p0 < len; p0 += 2 * width) {
+            const int na = min(width, len - p0);
+            const int nb = max(0, min(width, len - p0 - width));
+            const int *A = src + b + p0, *B = A + na;
+            int *o = dst + b + p0;
+            const int L = na + nb;
+            const int per = (L + blockDim.x - 1) / blockDim.x;
+            const int k0 = min(L, (int)threadIdx.x * per), k1 = min(L, k0 + per);
+            int i = co_rank(k0, A, na, B, nb), j = k0 - i;
+            for (int k = k0; k < k1; ++k) {
+                if (j >= nb || (i < na && A[i] < B[j])) o[k] = A[i++];
+                else o[k] = B[j++];
+            }
+        }
+        __syncthreads();
+        int *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != out) {
+        for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = src[b + q];
+    }
+    __syncthreads();
+}
+
 template <class Seg>
 __global__ void segsort_long_kernel(Seg seg, int *data, int *tmp, int *out,
                                     const int *__restrict__ long_list,
@@ -419,42 +470,7 @@ __global__ void segsort_long_kernel(Seg seg, int *data, int *tmp, int *out,
     const int nl = *long_count;
     for (int w = blockIdx.x; w < nl; w += gridDim.x) {
         const int s = long_list[w];
-        const int b = seg.begin(s), e = seg.end(s);
-        const int len = e - b;
-        if (len <= SEG_CHUNK) {
-            chunk_sort(data, b, len, sm);
-            if (out != data) {
-                for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = data[b + q];
-                __syncthreads();
-            }
-            continue;
-        }
-        for (int c0 = 0; c0 < len; c0 += SEG_CHUNK) chunk_sort(data, b + c0, min(SEG_CHUNK, len - c0), sm);
-        int *src = data, *dst = tmp;
-        for (int width = SEG_CHUNK; width < len; width *= 2) {
-            for (int p0 = 0; p0 < len; p0 += 2 * width) {
-                const int na = min(width, len - p0);
-                const int nb = max(0, min(width, len - p0 - width));
-                const int *A = src + b + p0, *B = A + na;
-                int *out = dst + b + p0;
-                const int L = na + nb;
-                const int per = (L + blockDim.x - 1) / blockDim.x;
-                const int k0 = min(L, (int)threadIdx.x * per), k1 = min(L, k0 + per);
-                int i = co_rank(k0, A, na, B, nb), j = k0 - i;
-                for (int k = k0; k < k1; ++k) {
-                    if (j >= nb || (i < na && A[i] < B[j])) out[k] = A[i++];
-                    else out[k] = B[j++];
-                }
-            }
-            __syncthreads();
-            int *t = src;
-            src = dst;
-            dst = t;
-        }
-        if (src != out) {
-            for (int q = threadIdx.x; q < len; q += blockDim.x) out[b + q] = src[b + q];
-        }
-        __syncthreads();
+        segsort_one(seg.begin(s), seg.end(s), data, tmp, out, sm);
     }
 }
 
@@ -471,6 +487,232 @@ struct RevSeg {   // reverse part of neighbour row s, clipped to the list capaci
     __device__ int end(int s) const { return min(nb_start[s + 1], cap); }
     __device__ int begin(int s) const { return min(nb_start[s] + own[s], end(s)); }
 };
+
+
+// ---------------------------------------------------------------------------
+// The whole sorting stage as one cooperative launch.  Its phases are the
+// kernels above, in the same order and with the same arithmetic (so keys,
+// bucket starts, permutation and statistics are bitwise those of the
+// multi-kernel path), separated by grid-wide barriers; a cooperative launch
+// keeps every block resident, so the barriers cannot wait on a block that
+// has not started.  Every phase is a grid-stride loop.
+//   A  zero the bucket and level statistics and the bucket counts; reduce
+//      the extremes of x, y, z, h (derived grid)
+//   B  every block derives the same grid from the extremes; bin (SP1)
+//   C  scan of the bucket counts (SP2, SP3): chunk totals, then each block
+//      scans its chunk from the total of the chunks before it
+//   D  scatter with the atomic cursor (SP4), which drives the counts back
+//      to zero
+//   E  rank inside the buckets; F  block sort of buckets over 64 members
+//   G  sorted copies and the statistics over the sorted order
+// The extremes are reduced as atomicMax of ~ordered(min) and ordered(max),
+// so 0 is the neutral value: the workspace starts zeroed, and block 0 puts
+// them back to 0 once every block has read them (phase C).
+// ---------------------------------------------------------------------------
+
+namespace cgf = cooperative_groups;
+
+constexpr int FS_THREADS = 256;
+
+__device__ __forceinline__ void block_max_to(unsigned v, unsigned *shared5, int slot, unsigned *global) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&shared5[slot], v);
+    __syncthreads();
+    if (threadIdx.x == 0 && shared5[slot]) atomicMax(global, shared5[slot]);
+}
+
+__global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
+    cgf::grid_group grid = cgf::this_grid();
+    __shared__ unsigned s_red[5];
+    __shared__ int s_warp[33];
+    __shared__ int s_cnt[kMaxLevels];
+    __shared__ unsigned s_hmax[kMaxLevels];
+    __shared__ int s_seg[SEG_CHUNK];
+    __shared__ long long s_pre;
+    const int tid = threadIdx.x;
+    const long long gtid = (long long)blockIdx.x * FS_THREADS + tid;
+    const long long gstride = (long long)gridDim.x * FS_THREADS;
+    const int n = a.n, M = 1 << a.log2_M;
+    if (tid < 5) s_red[tid] = 0u;
+    if (tid < kMaxLevels) {
+        s_cnt[tid] = 0;
+        s_hmax[tid] = 0u;
+    }
+    __syncthreads();
+
+    // A: zero the statistics and counts; reduce the extremes
+    for (long long q = gtid; q < M; q += gstride) {
+        a.count[q] = 0;
+        a.hmax_cell[q] = 0u;
+    }
+    for (long long q = gtid; q < (long long)(M / 16 + 1); q += gstride) a.occ[q] = 0u;
+    if (blockIdx.x == 0 && tid < kMaxLevels) {
+        a.lvl_count[tid] = 0;
+        a.lvl_hmax[tid] = 0u;
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.long_count = 0;
+    if (a.auto_grid) {
+        unsigned mx = 0u, my = 0u, mz = 0u, mh = 0u, Mh = 0u;
+        for (long long i = gtid; i < n; i += gstride) {
+            const float4 p = a.pos_h[i];
+            if (p.x == p.x && fabsf(p.x) < 3.0e38f) mx = max(mx, ~float_to_ordered(p.x));
+            if (p.y == p.y && fabsf(p.y) < 3.0e38f) my = max(my, ~float_to_ordered(p.y));
+            if (p.z == p.z && fabsf(p.z) < 3.0e38f) mz = max(mz, ~float_to_ordered(p.z));
+            if (p.w > 0.0f && p.w < 3.0e38f) {
+                mh = max(mh, ~float_to_ordered(p.w));
+                Mh = max(Mh, float_to_ordered(p.w));
+            }
+        }
+        block_max_to(mx, s_red, 0, &a.red[0]);
+        block_max_to(my, s_red, 1, &a.red[1]);
+        block_max_to(mz, s_red, 2, &a.red[2]);
+        block_max_to(mh, s_red, 3, &a.red[3]);
+        block_max_to(Mh, s_red, 4, &a.red[4]);
+    }
+    grid.sync();
+
+    // B: the grid, then the bucket of every particle and the counts
+    GridDev g = a.given;
+    if (a.auto_grid) {
+        const unsigned r[5] = {~a.red[0], ~a.red[1], ~a.red[2], ~a.red[3], a.red[4]};
+        g = grid_from_red(r, a.log2_M);
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.grid = g;
+    for (long long i = gtid; i < n; i += gstride) {
+        int l, cx, cy, cz;
+        const int k = bucket_of_particle(a.pos_h[i], a.sim_of ? a.sim_of[i] : 0, g, l, cx, cy, cz);
+        a.key[i] = k;
+        atomicAdd(&a.count[k], 1);
+    }
+    grid.sync();
+
+    // C: chunk totals of the counts, then each chunk's exclusive scan
+    const long long chunk = ((long long)M + gridDim.x - 1) / gridDim.x;
+    const long long c0 = (long long)blockIdx.x * chunk, c1 = min((long long)M, c0 + chunk);
+    {
+        int v = 0;
+        for (long long q = c0 + tid; q < c1; q += FS_THREADS) v += a.count[q];
+        int total;
+        block_excl_scan(v, s_warp, &total);
+        if (tid == 0) a.block_sums[blockIdx.x] = total;
+        if (blockIdx.x == 0 && tid < 5) a.red[tid] = 0u;   // every block has read the extremes
+    }
+    grid.sync();
+    {
+        int v = 0;
+        for (int b = tid; b < (int)blockIdx.x; b += FS_THREADS) v += a.block_sums[b];
+        int before;
+        block_excl_scan(v, s_warp, &before);
+        int carry = before;
+        for (long long t0 = c0; t0 < c1; t0 += FS_THREADS) {
+            const long long q = t0 + tid;
+            const int x = q < c1 ? a.count[q] : 0;
+            int tot;
+            const int ex = block_excl_scan(x, s_warp, &tot);
+            if (q < c1) a.start[q] = carry + ex;
+            carry += tot;
+        }
+        if (blockIdx.x == gridDim.x - 1 && tid == 0) a.start[M] = carry;
+    }
+    grid.sync();
+
+    // D: counting-sort scatter (the cursor drives the counts back to zero)
+    for (long long i = gtid; i < n; i += gstride) {
+        const int k = a.key[i];
+        const int pos = atomicSub(&a.count[k], 1) - 1;
+        a.tmp[a.start[k] + pos] = (int)i;
+    }
+    grid.sync();
+
+    // E: rank inside the buckets (ascending original index)
+    for (long long i = gtid; i < n; i += gstride) {
+        const int k = a.key[i];
+        const int s = a.start[k], e = a.start[k + 1];
+        if (e - s > RANK_MAX) {
+            if (a.tmp[s] == (int)i) a.long_list[atomicAdd(a.long_count, 1)] = k;
+            continue;
+        }
+        int r = 0;
+        for (int q = s; q < e; ++q) r += a.tmp[q] < (int)i;
+        a.perm[s + r] = (int)i;
+    }
+    grid.sync();
+
+    // F: the long buckets, one block each
+    {
+        const int nl = *a.long_count;
+        for (int w = blockIdx.x; w < nl; w += gridDim.x) {
+            const int k = a.long_list[w];
+            segsort_one(a.start[k], a.start[k + 1], a.tmp, a.perm, a.perm, s_seg);
+        }
+    }
+    grid.sync();
+
+    // G: sorted copies and the statistics (warp-uniform trip count, so the
+    // warp-wide matches see every lane)
+    const int lane = tid & 31;
+    for (long long w0 = gtid - lane; w0 < n; w0 += gstride) {
+        const long long j = w0 + lane;
+        int l = -1, k = -1;
+        unsigned hb = 0u, sbit = 0xffffffffu;
+        if (j < n) {
+            const int i = a.perm[j];
+            const float4 p = a.pos_h[i];
+            a.pos_h_s[j] = p;
+            const int sim = a.sim_of ? a.sim_of[i] : 0;
+            if (a.sim_s) a.sim_s[j] = sim;
+            int cx, cy, cz;
+            k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
+            hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;
+            if (a.occ)
+                sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
+                                 l + kMaxLevels * sim, a.log2_B);
+        }
+        {
+            const unsigned peers = __match_any_sync(0xffffffffu, k);
+            const unsigned m = __reduce_max_sync(peers, hb);
+            if (k >= 0 && lane == __ffs(peers) - 1 && m > 0u) atomicMax(&a.hmax_cell[k], m);
+        }
+        if (a.occ) {
+            const unsigned peers = __match_any_sync(0xffffffffu, sbit);
+            if (k >= 0 && lane == __ffs(peers) - 1) atomicOr(&a.occ[sbit >> 5], 1u << (sbit & 31));
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        const unsigned hpeer = __reduce_max_sync(peers, hb);
+        if (l >= 0 && lane == __ffs(peers) - 1) {
+            atomicAdd(&s_cnt[l], __popc(peers));
+            atomicMax(&s_hmax[l], hpeer);
+        }
+    }
+    __syncthreads();
+    if (tid < kMaxLevels && s_cnt[tid]) {
+        atomicAdd(&a.lvl_count[tid], s_cnt[tid]);
+        atomicMax(&a.lvl_hmax[tid], s_hmax[tid]);
+    }
+    (void)s_pre;
+}
+
+int launch_sort_fused(const SortArgs &a, cudaStream_t st) {
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sort_fused_kernel, FS_THREADS, 0) !=
+            cudaSuccess)
+            return SPH_ERR_CUDA;
+        blocks_per_sm = occ;
+    }
+    if (blocks_per_sm < 1) return SPH_ERR_CUDA;
+    const long long want = std::max<long long>(1, ((long long)std::max(a.n, 1 << a.log2_M) + FS_THREADS - 1) /
+                                                      FS_THREADS);
+    const int grid = (int)std::min<long long>({want, (long long)blocks_per_sm * device_num_sms(),
+                                               (long long)a.block_sums_cap});
+    SortArgs args = a;
+    void *params[] = {&args};
+    SPH_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)sort_fused_kernel, dim3(grid), dim3(FS_THREADS),
+                                             params, 0, st));
+    note_launch();
+    return SPH_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Host launchers.

@@ -116,6 +116,7 @@ def lib():
             "sph_ctx_destroy": (_I, [_P]),
             "sph_ctx_set_params": (_I, [_P, ctypes.POINTER(SphParams)]),
             "sph_ctx_set_lanes": (_I, [_P, _I]),
+            "sph_ctx_set_sort_fused": (_I, [_P, _I]),
             "sph_ctx_device_status": (_I, [_P, _P, ctypes.POINTER(_I)]),
             "sph_ctx_get_grid": (_I, [_P, _P, ctypes.POINTER(SphGrid)]),
             "sph_ctx_nb_total": (_I, [_P, _P, ctypes.POINTER(_I64)]),
@@ -263,6 +264,11 @@ class Ctx:
         """Lanes per neighbour row in the density / force kernels (1, 2, 4, 8)."""
         _check("sph_ctx_set_lanes", lib().sph_ctx_set_lanes(self.handle, int(lanes)))
         self.lanes = int(lanes)
+
+    def set_sort_fused(self, fused):
+        """1: the sorting stage as one cooperative launch (default); 0: as a
+        sequence of kernels (the same results)."""
+        _check("sph_ctx_set_sort_fused", lib().sph_ctx_set_sort_fused(self.handle, int(fused)))
 
     def device_status(self, stream=None):
         f = _I()

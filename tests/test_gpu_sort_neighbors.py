@@ -313,3 +313,48 @@ def test_group_wider_than_one_row_cap_walks_row_by_row(orc):
     ctx, perm = _check_sort(orc, ph, grid, ctx)
     start, idx, sets = _check_lists(orc, ph, ctx, perm)
     assert sets == {0: {1}, 1: {0}}
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_one_launch_sort_equals_the_kernel_sequence(orc, batched):
+    # the sorting stage as one cooperative launch and as its sequence of
+    # kernels: keys, starts, permutation, derived grid and the neighbour
+    # lists built from each (which read the bucket, level and occupancy
+    # statistics) are bitwise equal, and equal to the oracle's sort
+    torch = need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.sim import assemble_batch
+    if batched:
+        lst = [ics.two_halo(3000, 100, seed=81), ics.single_halo(5000, 0, seed=82),
+               ics.single_halo(700, 50, seed=83)]
+        ic, go, do, so = assemble_batch(lst)
+        ng = int(ic["n_gas"])
+        ph = pos_h_of(ic["r"][:ng], ic["h"])
+        batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
+    else:
+        d = ics.two_halo(40000, 0, seed=84)
+        ph = pos_h_of(d["r"], d["h"])
+        ng = len(ph)
+        batch = None
+    out = []
+    for fused in (1, 0, 1):
+        ctx = _ctx(ng)
+        ctx.set_sort_fused(fused)
+        if batch is not None:
+            nv.sph_ctx_set_batch(ctx, batch)
+        _, key, start, perm = _sort(ph, ctx=ctx)
+        grid = ctx.grid()
+        st, idx = _lists(ctx, ng)
+        out.append((key, start, perm, grid, st, idx))
+    for a, b in ((out[0], out[1]), (out[2], out[1])):
+        for x, y in zip(a, b):
+            if isinstance(x, dict):
+                assert x == y
+            else:
+                assert np.array_equal(x, y)
+    if not batched:
+        _, _, okey = orc.bin_particles(ph, out[0][3])
+        _, ostart, operm = orc.counting_sort(okey, 1 << out[0][3]["log2_M"])
+        assert np.array_equal(out[0][0], okey)
+        assert np.array_equal(out[0][1], ostart)
+        assert np.array_equal(out[0][2], operm)
