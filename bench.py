@@ -421,8 +421,9 @@ def run_ours(args):
     ips = float(n) * n / (gfc_ms / 1e3)
     if "grav_work" in sim.t and nv.pp_gravity_pairs_eligible(n, sim.params["eps"], sim.grav_flags):
         kernel = "pp_gravity_pairs_kernel"
-        plan = {"scheme": "each unordered pair once (Newton's third law)", "block": 1024,
-                "targets_per_thread": 8}
+        th, R, lg = nv.pp_gravity_pairs_get_plan(n)
+        plan = {"scheme": "each unordered pair once (Newton's third law)", "block": th * R,
+                "threads": th, "targets_per_thread": R, "super_tile_log2": lg}
     else:
         kernel = "pp_gravity_kernel"
         R, S = nv.sph_gravity_plan(n)
@@ -548,13 +549,16 @@ def run_ensemble(args):
         return e0.elapsed_time(e1)
 
     # (a) batched
+    from paper_1807_08116_gb300.tune import tune_batch, tune_grid, tune_lanes
     bsim = Simulation(ic, batch_offsets=(go, do, so))
     bsim.initial_rhs()
     pairs = "grav_work" in bsim.t   # pair-once gravity over all simulations' tiles
     best_R, tune = None, None
     if not pairs:
-        from paper_1807_08116_gb300.tune import tune_batch
         best_R, tune = tune_batch(bsim.batch, bsim.t["pos_m"], reps=3)
+    # the SPH knobs of the batch: grid cell size and lanes per neighbour row
+    best_shift, tune_shift = tune_grid(bsim, reps=3)
+    best_lanes, tune_l = tune_lanes(bsim, reps=3)
     for _ in range(args.warmup):
         bsim.step(dt)
     bsim.capture(dt)
@@ -605,7 +609,9 @@ def run_ensemble(args):
                    "n_total": n_tot, "n_sims": args.n_sims, "cuda_graph": True,
                    "gravity": ("pair-once, one launch over the tiles of every simulation" if pairs
                                else "one-sided persistent work queue"),
-                   "gravity_units_R": best_R, "autotune_ms": tune},
+                   "gravity_units_R": best_R, "autotune_ms": tune,
+                   "tuned": {"grid_shift": best_shift, "grid_shift_ms": tune_shift,
+                             "lanes": best_lanes, "lanes_ms": tune_l}},
         "max_rel_position_diff_batched_vs_sequential": worst,
         "stage_ms_batched": stage_b,
         "interactions_per_step": float(sum(d["n"] ** 2 for d in lst)),
@@ -753,6 +759,11 @@ def run_gravity(args):
     n = d["n"]
     pairs = not args.one_sided and nv.pp_gravity_pairs_eligible(n, 0.01)
     work = nv.pp_gravity_pairs_workspace(n) if pairs else None
+    tuned = None
+    if pairs and args.tune:
+        from paper_1807_08116_gb300.tune import tune_pairs_plan
+        best, res = tune_pairs_plan(x, work, reps=2)
+        tuned = {"best": list(best), "ms": {str(list(k)): v for k, v in sorted(res.items())}}
 
     def launch():
         if pairs:
@@ -774,7 +785,9 @@ def run_gravity(args):
     ips = float(n) * n / (ms / 1e3)
     kernel = "pp_gravity_pairs_kernel" if pairs else "pp_gravity_kernel"
     if pairs:
-        plan = {"scheme": "each unordered pair once", "block": 1024, "targets_per_thread": 8}
+        th, R, lg = nv.pp_gravity_pairs_get_plan(n)
+        plan = {"scheme": "each unordered pair once", "block": th * R, "threads": th,
+                "targets_per_thread": R, "super_tile_log2": lg, "tuned": tuned}
     else:
         R, S = nv.sph_gravity_plan(n)
         plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
@@ -800,6 +813,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity")
     ap.add_argument("--one-sided", action="store_true",
                     help="--workload gravity: time the one-sided kernel instead of the pair-once one")
+    ap.add_argument("--tune", action="store_true",
+                    help="--workload gravity: time every pair-once plan first and keep the fastest")
     ap.add_argument("--shard", action="store_true",
                     help="--workload gravity: split the rows over the ranks (particle partition, "
                          "one all-gather of the sources per launch)")

@@ -101,6 +101,12 @@ int sph_ctx_destroy(sph_ctx *ctx);
  * order of the per-lane partial sums. */
 int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes);
 
+/* Octaves added to the finest cell size of the grid sph_bin_and_sort
+ * derives (h_grid == NULL): L0 = 2^(ceil(log2 min h) + shift), and as many
+ * levels as max h then needs; shift in [-4, 4], default 0.  A tuning knob of
+ * the neighbour search: any shift gives the same neighbour sets. */
+int sph_ctx_set_grid_shift(sph_ctx *ctx, int32_t shift);
+
 /* How sph_bin_and_sort runs the sorting stage: 1 (default) as one
  * cooperative launch whose phases are separated by grid-wide barriers, 0 as
  * a sequence of kernels (the form it also takes while `stream` is being
@@ -296,6 +302,20 @@ int sph_gravity_tune(int32_t R, int32_t S);
  * the fixed-point scale outside 2^-250..2^250. */
 int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float eps, float *d_acc_pot,
                      int32_t flags, void *d_work, size_t work_bytes, sph_stream_t stream);
+
+/* Launch plan of pp_gravity_pairs on one simulation (process-wide, for
+ * autotuning): `threads` per CTA and R targets per thread -- (128, 6),
+ * (128, 8), (128, 10) or (256, 8), i.e. blocks of 768, 1024, 1280 or 2048
+ * bodies -- and tiles visited in super-tiles of 2^super_log2_side blocks on a
+ * side (0..8; -1: chosen by size).  threads = 0 restores the default (128, 8,
+ * -1).  Results of different plans agree to force rounding (other block
+ * boundaries, so another summation order); one plan is bitwise reproducible.
+ * Batches (pp_gravity_pairs_batched) always use the default shape. */
+int pp_gravity_pairs_plan(int32_t threads, int32_t R, int32_t super_log2_side);
+
+/* The plan pp_gravity_pairs uses for n bodies: threads per CTA, targets per
+ * thread and the super-tile side (log2). */
+int pp_gravity_pairs_get_plan(int32_t n, int32_t *h_threads, int32_t *h_R, int32_t *h_super_log2);
 
 /* Scratch bytes of pp_gravity_pairs for n bodies (4096 + 32 n). */
 size_t pp_gravity_pairs_workspace_bytes(int32_t n);

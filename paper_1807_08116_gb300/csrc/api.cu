@@ -87,6 +87,7 @@ struct sph_ctx {
     int sorted_batched;        // the last sort used the batch's simulation map
     int hydro_lanes;           // lanes per row in DC / HFC (1, 2, 4 or 8)
     int sort_fused;            // 1: the sorting stage as one cooperative launch
+    int grid_shift;            // octaves added to the derived finest cell size
     const sph_batch *batch;    // NULL: one simulation
 };
 
@@ -228,6 +229,12 @@ extern "C" int sph_ctx_set_lanes(sph_ctx *ctx, int32_t lanes) {
     return SPH_OK;
 }
 
+extern "C" int sph_ctx_set_grid_shift(sph_ctx *ctx, int32_t shift) {
+    if (!ctx || shift < -4 || shift > 4) return SPH_ERR_INVALID_ARG;
+    ctx->grid_shift = shift;
+    return SPH_OK;
+}
+
 extern "C" int sph_ctx_set_sort_fused(sph_ctx *ctx, int32_t fused) {
     if (!ctx || (fused != 0 && fused != 1)) return SPH_ERR_INVALID_ARG;
     ctx->sort_fused = fused;
@@ -312,6 +319,7 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
         fa.n = n_gas;
         fa.log2_M = ctx->log2_M;
         fa.auto_grid = h_grid ? 0 : 1;
+        fa.grid_shift = ctx->grid_shift;
         if (h_grid)
             fa.given = GridDev{h_grid->x0, h_grid->y0, h_grid->z0, h_grid->log2_L0, h_grid->n_levels,
                                h_grid->log2_M};
@@ -338,7 +346,7 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
     }
     if (!fused) {
         if (h_grid) rc = launch_grid_set(*h_grid, ctx->grid, st);
-        else rc = launch_grid_auto(pos, n_gas, ctx->red, ctx->log2_M, ctx->grid, st);
+        else rc = launch_grid_auto(pos, n_gas, ctx->red, ctx->log2_M, ctx->grid, st, ctx->grid_shift);
         if (rc) return rc;
         // SP0: zero the per-bucket and per-level arrays
         SPH_CUDA_TRY(cudaMemsetAsync(ctx->count, 0, sizeof(int) * (size_t)M, st));

@@ -52,19 +52,30 @@
 
 namespace sphgb {
 
-constexpr int GP_THREADS = 128;
-constexpr int GP_RP = 4;                      // target pairs per thread
-constexpr int GP_R = 2 * GP_RP;               // targets per thread
-constexpr int GP_B = GP_THREADS * GP_R;       // bodies per block
-constexpr int GP_WARPS = GP_THREADS / 32;
 constexpr int GP_SLAB = 256;                  // sources per cross-warp reduction
 constexpr int GP_MASS_BLOCKS = 256;
-constexpr int GP_SMEM_DUP = 2 * GP_B * 16;                  // (x, x, y, y), (z, z, m, m)
-constexpr int GP_SMEM_PART = GP_WARPS * GP_SLAB * 4 * 4;    // warp sums of a slab
-constexpr int GP_SMEM_IDX = 2 * GP_B * 4;                  // global indices of the tile
-constexpr int GP_SMEM = GP_SMEM_DUP + GP_SMEM_PART + GP_SMEM_IDX;
-static_assert(GP_SMEM <= 227 * 1024, "shared memory of the pair kernel");
-static_assert(GP_B % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
+
+// Shape of a tile: THREADS threads, RP target pairs (2 RP targets) per
+// thread, blocks of B = THREADS x 2 RP bodies; shared memory holds the source
+// block expanded to (x, x, y, y), (z, z, m, m), the warp sums of one slab and
+// the global indices of the tile's bodies.
+template <int THREADS, int RP>
+struct PairsShape {
+    static constexpr int kB = THREADS * 2 * RP;
+    static constexpr int kWarps = THREADS / 32;
+    static constexpr int kSmemDup = 2 * kB * 16;
+    static constexpr int kSmemPart = kWarps * GP_SLAB * 4 * 4;
+    static constexpr int kSmemIdx = 2 * kB * 4;
+    static constexpr int kSmem = kSmemDup + kSmemPart + kSmemIdx;
+    static_assert(kSmem <= 227 * 1024, "shared memory of the pair kernel");
+    static_assert(kB % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
+};
+
+// The default shape (128 threads, 8 targets each, blocks of 1024), which a
+// batch always uses; a single simulation takes the plan of pp_gravity_pairs_plan.
+constexpr int GP_THREADS = 128;
+constexpr int GP_RP = 4;
+constexpr int GP_B = PairsShape<GP_THREADS, GP_RP>::kB;
 
 // Fixed-point scale of one simulation: sums of g are integers times 2^e_acc,
 // sums of phi integers times 2^e_pot.
@@ -207,13 +218,13 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, float s1, float 
 // One slab (GP_SLAB sources starting at s0) of a tile.  SYM: also collect
 // the sums of the sources (off-diagonal tiles) into wpart[GP_SLAB][NC].
 // ---------------------------------------------------------------------------
-template <bool SYM, bool POT>
+template <bool SYM, bool POT, int THREADS, int RP>
 __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const float4 *__restrict__ dB,
-                                          int s0, int lane, const float2 (&nx)[GP_RP],
-                                          const float2 (&ny)[GP_RP], const float2 (&nz)[GP_RP],
-                                          const float2 (&mi)[GP_RP], float2 e2, float2 (&ax)[GP_RP],
-                                          float2 (&ay)[GP_RP], float2 (&az)[GP_RP],
-                                          float2 (&ap)[GP_RP], float *__restrict__ wpart, int tid) {
+                                          int s0, int lane, const float2 (&nx)[RP],
+                                          const float2 (&ny)[RP], const float2 (&nz)[RP],
+                                          const float2 (&mi)[RP], float2 e2, float2 (&ax)[RP],
+                                          float2 (&ay)[RP], float2 (&az)[RP],
+                                          float2 (&ap)[RP], float *__restrict__ wpart, int tid) {
     constexpr int NC = POT ? 4 : 3;
     for (int c = 0; c < GP_SLAB / 32; ++c) {
         float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;   // sums of the source this lane holds
@@ -228,7 +239,7 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
             float2 tx = make_float2(cx, 0.f), ty = make_float2(cy, 0.f), tz = make_float2(cz, 0.f);
             float2 tp = make_float2(cp, 0.f);
 #pragma unroll
-            for (int p = 0; p < GP_RP; ++p) {
+            for (int p = 0; p < RP; ++p) {
                 const float2 dx = __fadd2_rn(qx, nx[p]);
                 const float2 dy = __fadd2_rn(qy, ny[p]);
                 const float2 dz = __fadd2_rn(qz, nz[p]);
@@ -240,8 +251,8 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
                     // diagonal tile: leave j = i out of the potential (targets
                     // 2p and 2p + 1 of this thread are block entries
                     // tid + 2p 256 and tid + (2p + 1) 256)
-                    if (s == tid + (2 * p) * GP_THREADS) inv.x = 0.f;
-                    if (s == tid + (2 * p + 1) * GP_THREADS) inv.y = 0.f;
+                    if (s == tid + (2 * p) * THREADS) inv.x = 0.f;
+                    if (s == tid + (2 * p + 1) * THREADS) inv.y = 0.f;
                 }
                 const float2 w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
                 const float2 si = __fmul2_rn(w, qm);
@@ -281,19 +292,21 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
 // In a batch, the global index of every target and source of the tile (-1
 // for padding) is kept in shared memory for the atomics; one simulation
 // computes them (the shared-memory form cost 1.5% there).
-template <bool POT, bool BATCH>
-__global__ void __launch_bounds__(GP_THREADS, 1)
+template <bool POT, bool BATCH, int THREADS, int RP>
+__global__ void __launch_bounds__(THREADS, 1)
 pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
                         const int4 *__restrict__ sims, const long long *__restrict__ tile_off,
                         int n_sims, float eps2, const PairsScale *__restrict__ scales,
                         unsigned long long *__restrict__ acc) {
     constexpr int NC = POT ? 4 : 3;
+    using Sh = PairsShape<THREADS, RP>;
+    constexpr int B = Sh::kB;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *dA = reinterpret_cast<float4 *>(smem);
-    float4 *dB = dA + GP_B;
-    float *part = reinterpret_cast<float *>(dB + GP_B);                   // [warp][slab][NC]
-    int *sidx = reinterpret_cast<int *>(smem + GP_SMEM_DUP + GP_SMEM_PART);  // [GP_B] sources
-    int *tidx = sidx + GP_B;                                               // [GP_B] targets
+    float4 *dB = dA + B;
+    float *part = reinterpret_cast<float *>(dB + B);                   // [warp][slab][NC]
+    int *sidx = reinterpret_cast<int *>(smem + Sh::kSmemDup + Sh::kSmemPart);  // [B] sources
+    int *tidx = sidx + B;                                               // [B] targets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int I, J, g0 = 0, ng = n, d0 = 0, ns = n, sim = 0;
     if (BATCH) {
@@ -315,12 +328,12 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
         return;
     }
     auto global_of = [&](int v) { return v < ng ? g0 + v : d0 + (v - ng); };
-    const int cnt = min(GP_B, ns - J * GP_B);
-    for (int q = tid; q < GP_B; q += GP_THREADS) {
+    const int cnt = min(B, ns - J * B);
+    for (int q = tid; q < B; q += THREADS) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         int gi = -1;
         if (q < cnt) {
-            gi = global_of(J * GP_B + q);
+            gi = global_of(J * B + q);
             v = pos[gi];
         }
         if (BATCH) sidx[q] = gi;
@@ -328,11 +341,11 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
         dB[q] = make_float4(v.z, v.z, v.w, v.w);
     }
     // targets k of this thread: block entries tid + k 256; pair p = (2p, 2p + 1)
-    float2 nx[GP_RP], ny[GP_RP], nz[GP_RP], mi[GP_RP], ax[GP_RP], ay[GP_RP], az[GP_RP], ap[GP_RP];
+    float2 nx[RP], ny[RP], nz[RP], mi[RP], ax[RP], ay[RP], az[RP], ap[RP];
 #pragma unroll
-    for (int p = 0; p < GP_RP; ++p) {
-        const int ka = tid + (2 * p) * GP_THREADS, kb = ka + GP_THREADS;
-        const int va = I * GP_B + ka, vb = I * GP_B + kb;
+    for (int p = 0; p < RP; ++p) {
+        const int ka = tid + (2 * p) * THREADS, kb = ka + THREADS;
+        const int va = I * B + ka, vb = I * B + kb;
         const int ia = va < ns ? global_of(va) : -1, ib = vb < ns ? global_of(vb) : -1;
         if (BATCH) {
             tidx[ka] = ia;
@@ -353,16 +366,16 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
     float *wpart = part + warp * GP_SLAB * NC;
     if (I != J) {
         for (int s0 = 0; s0 < cnt; s0 += GP_SLAB) {   // sources past cnt are massless padding
-            ring_slab<true, POT>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+            ring_slab<true, POT, THREADS, RP>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
             __syncthreads();
-            for (int q = tid; q < GP_SLAB * NC; q += GP_THREADS) {
+            for (int q = tid; q < GP_SLAB * NC; q += THREADS) {
                 float v = 0.f;
 #pragma unroll
-                for (int w = 0; w < GP_WARPS; ++w) v = __fadd_rn(v, part[w * GP_SLAB * NC + q]);
+                for (int w = 0; w < Sh::kWarps; ++w) v = __fadd_rn(v, part[w * GP_SLAB * NC + q]);
                 const int comp = q % NC;
                 int j;
                 if (BATCH) j = sidx[s0 + q / NC];
-                else j = (J * GP_B + s0 + q / NC < n) ? J * GP_B + s0 + q / NC : -1;
+                else j = (J * B + s0 + q / NC < n) ? J * B + s0 + q / NC : -1;
                 if (j >= 0)
                     atomicAdd(&acc[(size_t)j * 4 + comp],
                               comp < 3 ? to_fixed(-v, sa1, sa2) : to_fixed(v, sp1, sp2));
@@ -371,18 +384,18 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
         }
     } else {
         for (int s0 = 0; s0 < cnt; s0 += GP_SLAB)
-            ring_slab<false, POT>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+            ring_slab<false, POT, THREADS, RP>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
     }
     // the tile's sums of its targets
 #pragma unroll
-    for (int p = 0; p < GP_RP; ++p) {
+    for (int p = 0; p < RP; ++p) {
         int ia, ib;
         if (BATCH) {
-            ia = tidx[tid + (2 * p) * GP_THREADS];
-            ib = tidx[tid + (2 * p + 1) * GP_THREADS];
+            ia = tidx[tid + (2 * p) * THREADS];
+            ib = tidx[tid + (2 * p + 1) * THREADS];
         } else {
-            ia = I * GP_B + tid + (2 * p) * GP_THREADS;
-            ib = ia + GP_THREADS;
+            ia = I * B + tid + (2 * p) * THREADS;
+            ib = ia + THREADS;
             if (ia >= n) ia = -1;
             if (ib >= n) ib = -1;
         }
@@ -437,22 +450,65 @@ static int g_pairs_status = SPH_OK;
 static int g_pairs_min_n = 16384;   // measured crossover with the one-sided kernel
 static std::mutex g_pairs_mutex;
 
+// Launch plan of a single simulation's tiles: threads per CTA, target pairs
+// per thread, super-tile side 2^lg blocks (lg < 0: by size, super_log2).
+struct PairsPlan {
+    int threads, rp, lg;
+};
+static PairsPlan g_pairs_plan{GP_THREADS, GP_RP, -1};
+
+using PairsKernel = void (*)(const float4 *, int, int, int, const int4 *, const long long *, int,
+                             float, const PairsScale *, unsigned long long *);
+
+struct PairsVariant {
+    PairsKernel k;
+    int smem;
+};
+
+template <int THREADS, int RP>
+static PairsVariant pairs_variant(bool pot, bool batch) {
+    const int smem = PairsShape<THREADS, RP>::kSmem;
+    if (pot) return {batch ? pp_gravity_pairs_kernel<true, true, THREADS, RP>
+                           : pp_gravity_pairs_kernel<true, false, THREADS, RP>, smem};
+    return {batch ? pp_gravity_pairs_kernel<false, true, THREADS, RP>
+                  : pp_gravity_pairs_kernel<false, false, THREADS, RP>, smem};
+}
+
+// The shapes the plan may name: (128, 3), (128, 4), (128, 5) and (256, 4),
+// i.e. blocks of 768, 1024, 1280 and 2048 bodies.
+static bool pairs_shape_ok(int threads, int rp) {
+    return (threads == 128 && rp >= 3 && rp <= 5) || (threads == 256 && rp == 4);
+}
+
+static PairsVariant pairs_pick(int threads, int rp, bool pot, bool batch) {
+    if (threads == 256) return pairs_variant<256, 4>(pot, batch);
+    if (rp == 3) return pairs_variant<128, 3>(pot, batch);
+    if (rp == 5) return pairs_variant<128, 5>(pot, batch);
+    return pairs_variant<128, 4>(pot, batch);
+}
+
 static void pairs_init() {
-    const void *k[4] = {(const void *)pp_gravity_pairs_kernel<false, false>,
-                        (const void *)pp_gravity_pairs_kernel<true, false>,
-                        (const void *)pp_gravity_pairs_kernel<false, true>,
-                        (const void *)pp_gravity_pairs_kernel<true, true>};
-    for (const void *f : k)
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM) !=
-            cudaSuccess)
-            g_pairs_status = SPH_ERR_CUDA;
+    const int shapes[4][2] = {{128, 3}, {128, 4}, {128, 5}, {256, 4}};
+    for (auto &sh : shapes)
+        for (int f = 0; f < 4; ++f) {
+            const PairsVariant v = pairs_pick(sh[0], sh[1], f & 1, f & 2);
+            if (cudaFuncSetAttribute((const void *)v.k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     v.smem) != cudaSuccess)
+                g_pairs_status = SPH_ERR_CUDA;
+        }
+}
+
+static PairsPlan pairs_plan() {
+    std::lock_guard<std::mutex> lock(g_pairs_mutex);
+    return g_pairs_plan;
 }
 
 // The launches of one evaluation over n bodies: zero the scratch, the scale,
-// the tiles (one simulation: nb blocks in super-tile order; a batch: n_ctas
-// tiles described by sims / tile_off), then the fixed-point totals -> out.
+// the tiles (one simulation: nb blocks of the plan's shape in super-tiles of
+// 2^lg; a batch: n_ctas tiles of the default shape described by sims /
+// tile_off), then the fixed-point totals -> out.
 static int pairs_launch(const float4 *pos, int n, int n_gas, float G, float eps, float4 *out,
-                        int flags, void *d_work, int nb, const int4 *sims,
+                        int flags, void *d_work, int nb, int lg, PairsPlan plan, const int4 *sims,
                         const long long *tile_off, int n_sims, long long n_ctas,
                         PairsScale *batch_scales, cudaStream_t st) {
     std::call_once(g_pairs_once, pairs_init);
@@ -476,11 +532,10 @@ static int pairs_launch(const float4 *pos, int n, int n_gas, float G, float eps,
         pairs_scale_kernel<<<1, GP_MASS_BLOCKS, 0, st>>>(eps, hdr, flags_dev);
         scales = &hdr->scale;
     }
-    auto k = pot ? (batch ? pp_gravity_pairs_kernel<true, true> : pp_gravity_pairs_kernel<true, false>)
-                 : (batch ? pp_gravity_pairs_kernel<false, true> : pp_gravity_pairs_kernel<false, false>);
+    const PairsVariant v = pairs_pick(plan.threads, plan.rp, pot, batch);
     if (n_ctas > 0)
-        k<<<(unsigned)n_ctas, GP_THREADS, GP_SMEM, st>>>(pos, n, nb, super_log2(nb), sims, tile_off,
-                                                        n_sims, eps2, scales, acc);
+        v.k<<<(unsigned)n_ctas, plan.threads, v.smem, st>>>(pos, n, nb, lg, sims, tile_off, n_sims, eps2,
+                                                            scales, acc);
     const long long *acc_s = reinterpret_cast<const long long *>(acc);
     auto f = pot ? (batch ? pairs_final_kernel<true, true> : pairs_final_kernel<true, false>)
                  : (batch ? pairs_final_kernel<false, true> : pairs_final_kernel<false, false>);
@@ -492,7 +547,8 @@ static int pairs_launch(const float4 *pos, int n, int n_gas, float G, float eps,
 
 size_t pairs_scale_bytes() { return sizeof(PairsScale); }
 
-// Tiles of simulation s with ns bodies: nb_s (nb_s + 1) / 2, nb_s = ceil(ns / 2048).
+// Tiles of simulation s with ns bodies in a batch (default shape):
+// nb_s (nb_s + 1) / 2, nb_s = ceil(ns / 1024).
 long long pairs_tiles(long long ns) {
     const long long nb = (ns + GP_B - 1) / GP_B;
     return nb * (nb + 1) / 2;
@@ -502,8 +558,9 @@ int launch_gravity_pairs_batched(const float4 *pos, int n, int n_gas, const int4
                                  const long long *d_tile_off, int n_sims, long long n_tiles,
                                  void *d_scales, float G, float eps, float4 *out, int flags,
                                  void *d_work, cudaStream_t st) {
-    return pairs_launch(pos, n, n_gas, G, eps, out, flags, d_work, 0, d_sims, d_tile_off, n_sims,
-                        n_tiles, static_cast<PairsScale *>(d_scales), st);
+    return pairs_launch(pos, n, n_gas, G, eps, out, flags, d_work, 0, 0,
+                        PairsPlan{GP_THREADS, GP_RP, -1}, d_sims, d_tile_off, n_sims, n_tiles,
+                        static_cast<PairsScale *>(d_scales), st);
 }
 
 }  // namespace sphgb
@@ -548,13 +605,39 @@ extern "C" int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float 
         (reinterpret_cast<uintptr_t>(d_acc_pot) & 15u) ||
         (reinterpret_cast<uintptr_t>(d_work) & 255u))
         return SPH_ERR_INVALID_ARG;
-    const long long nb = (n + GP_B - 1) / GP_B;
-    const int lg = super_log2(nb);
+    const PairsPlan plan = pairs_plan();
+    const int B = plan.threads * 2 * plan.rp;
+    const long long nb = (n + B - 1) / B;
+    const int lg = plan.lg >= 0 ? plan.lg : super_log2(nb);
     const long long nsb = (nb + (1ll << lg) - 1) >> lg;
     const long long n_ctas = (nsb * (nsb + 1) / 2) << (2 * lg);
     if (n_ctas > 0x7fffffffll)   // more than ~1.3e8 bodies: one CTA per tile no longer fits a grid
         return pp_gravity(d_pos_m, n, G, eps, d_acc_pot, flags, stream);
     return pairs_launch(reinterpret_cast<const float4 *>(d_pos_m), n, n, G, eps,
-                        reinterpret_cast<float4 *>(d_acc_pot), flags, d_work, (int)nb, nullptr,
-                        nullptr, 1, n_ctas, nullptr, (cudaStream_t)stream);
+                        reinterpret_cast<float4 *>(d_acc_pot), flags, d_work, (int)nb, lg, plan,
+                        nullptr, nullptr, 1, n_ctas, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int pp_gravity_pairs_plan(int32_t threads, int32_t R, int32_t super_log2_side) {
+    if (threads == 0) {
+        std::lock_guard<std::mutex> lock(g_pairs_mutex);
+        g_pairs_plan = PairsPlan{GP_THREADS, GP_RP, -1};
+        return SPH_OK;
+    }
+    if ((R & 1) || !pairs_shape_ok(threads, R / 2) || super_log2_side < -1 || super_log2_side > 8)
+        return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_pairs_mutex);
+    g_pairs_plan = PairsPlan{threads, R / 2, super_log2_side};
+    return SPH_OK;
+}
+
+extern "C" int pp_gravity_pairs_get_plan(int32_t n, int32_t *h_threads, int32_t *h_R,
+                                         int32_t *h_super_log2) {
+    if (n < 0 || !h_threads || !h_R || !h_super_log2) return SPH_ERR_INVALID_ARG;
+    const PairsPlan plan = pairs_plan();
+    const long long nb = ((long long)n + plan.threads * 2 * plan.rp - 1) / (plan.threads * 2 * plan.rp);
+    *h_threads = plan.threads;
+    *h_R = 2 * plan.rp;
+    *h_super_log2 = plan.lg >= 0 ? plan.lg : super_log2(nb);
+    return SPH_OK;
 }

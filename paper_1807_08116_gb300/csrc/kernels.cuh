@@ -14,8 +14,9 @@ int launch_sort_buckets(const int *key, int n, const int *start, int *unordered,
                         int *long_list, int *long_count, cudaStream_t st);
 int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int *data, int *tmp,
                         int *long_list, int *long_count, cudaStream_t st);
+// shift: octaves added to the derived finest cell size (0: L0 = 2^ceil(log2 min h))
 int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
-                     cudaStream_t st);
+                     cudaStream_t st, int shift = 0);
 int launch_grid_set(const SphGrid &h, GridDev *grid, cudaStream_t st);
 int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *grid, int *key,
                int *count, cudaStream_t st);
@@ -34,6 +35,7 @@ struct SortArgs {
     int n;
     int log2_M;
     int auto_grid;          // 1: derive the grid; 0: use `given`
+    int grid_shift;         // octaves added to the derived finest cell size
     GridDev given;
     unsigned *red;          // [5] extremes, 0 between calls
     GridDev *grid;          // out

@@ -79,7 +79,7 @@ __device__ __forceinline__ int ceil_log2_pos(float v) {
 
 // The grid from the reduced extremes: red[0..3] ordered-min of x, y, z, h
 // (0xffffffff: none), red[4] ordered-max of h (0: none).
-__device__ __forceinline__ GridDev grid_from_red(const unsigned red[5], int log2_M) {
+__device__ __forceinline__ GridDev grid_from_red(const unsigned red[5], int log2_M, int shift) {
     float mins[3];
     for (int d = 0; d < 3; ++d) {
         float v = red[d] == 0xffffffffu ? 0.0f : ordered_to_float(red[d]);
@@ -87,7 +87,8 @@ __device__ __forceinline__ GridDev grid_from_red(const unsigned red[5], int log2
     }
     float hmin = red[3] == 0xffffffffu ? 1.0f : ordered_to_float(red[3]);
     float hmax = red[4] == 0u ? hmin : ordered_to_float(red[4]);
-    int l0 = ceil_log2_pos(hmin);
+    // shift moves the finest cell size by whole octaves (a tuning knob)
+    int l0 = ceil_log2_pos(hmin) + shift;
     l0 = max(-100, min(100, l0));
     int top = ceil_log2_pos(hmax) - l0;   // levels above L0 needed for hmax
     int nl = 1 + max(0, top);
@@ -102,10 +103,10 @@ __device__ __forceinline__ GridDev grid_from_red(const unsigned red[5], int log2
     return g;
 }
 
-__global__ void grid_finalize_kernel(const unsigned *red, int log2_M, GridDev *grid) {
+__global__ void grid_finalize_kernel(const unsigned *red, int log2_M, int shift, GridDev *grid) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const unsigned r[5] = {red[0], red[1], red[2], red[3], red[4]};
-    *grid = grid_from_red(r, log2_M);
+    *grid = grid_from_red(r, log2_M, shift);
 }
 
 __global__ void grid_set_kernel(GridDev g, GridDev *grid) {
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
     GridDev g = a.given;
     if (a.auto_grid) {
         const unsigned r[5] = {~a.red[0], ~a.red[1], ~a.red[2], ~a.red[3], a.red[4]};
-        g = grid_from_red(r, a.log2_M);
+        g = grid_from_red(r, a.log2_M, a.grid_shift);
     }
     if (blockIdx.x == 0 && tid == 0) *a.grid = g;
     for (long long i = gtid; i < n; i += gstride) {
@@ -760,14 +761,14 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
 }
 
 int launch_grid_auto(const float4 *pos_h, int n, unsigned *red, int log2_M, GridDev *grid,
-                     cudaStream_t st) {
+                     cudaStream_t st, int shift) {
     const unsigned init[5] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu, 0u};
     // red is reset by a tiny kernel so the sequence stays capturable
     grid_reset_red(red, init, st);
     // a few resident blocks per SM of this device, each striding over the input
     unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4u * (unsigned)device_num_sms());
     if (n > 0) grid_reduce_kernel<<<nb, 256, 0, st>>>(pos_h, n, red);
-    grid_finalize_kernel<<<1, 32, 0, st>>>(red, log2_M, grid);
+    grid_finalize_kernel<<<1, 32, 0, st>>>(red, log2_M, shift, grid);
     note_launch(n > 0 ? 3 : 2);
     SPH_LAUNCH_CHECK();
     return SPH_OK;

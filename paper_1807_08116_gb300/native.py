@@ -117,6 +117,10 @@ def lib():
             "sph_ctx_set_params": (_I, [_P, ctypes.POINTER(SphParams)]),
             "sph_ctx_set_lanes": (_I, [_P, _I]),
             "sph_ctx_set_sort_fused": (_I, [_P, _I]),
+            "sph_ctx_set_grid_shift": (_I, [_P, _I]),
+            "pp_gravity_pairs_plan": (_I, [_I, _I, _I]),
+            "pp_gravity_pairs_get_plan": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                               ctypes.POINTER(_I)]),
             "sph_ctx_device_status": (_I, [_P, _P, ctypes.POINTER(_I)]),
             "sph_ctx_get_grid": (_I, [_P, _P, ctypes.POINTER(SphGrid)]),
             "sph_ctx_nb_total": (_I, [_P, _P, ctypes.POINTER(_I64)]),
@@ -270,6 +274,11 @@ class Ctx:
         sequence of kernels (the same results)."""
         _check("sph_ctx_set_sort_fused", lib().sph_ctx_set_sort_fused(self.handle, int(fused)))
 
+    def set_grid_shift(self, shift):
+        """Octaves added to the finest cell size of the derived grid."""
+        _check("sph_ctx_set_grid_shift", lib().sph_ctx_set_grid_shift(self.handle, int(shift)))
+        self.grid_shift = int(shift)
+
     def device_status(self, stream=None):
         f = _I()
         rc = lib().sph_ctx_device_status(self.handle, _stream(stream), ctypes.byref(f))
@@ -392,6 +401,20 @@ def pp_gravity_pairs(pos_m, acc_pot, work, G=1.0, eps=0.01, flags=0, stream=None
                                 float(eps), _ptr(acc_pot, torch.float32, (n, 4), "acc_pot"),
                                 int(flags), wp, wb, _stream(stream))
     _check("pp_gravity_pairs", rc)
+
+
+def pp_gravity_pairs_plan(threads=0, R=8, super_log2=-1):
+    """Fix the launch plan of the single-simulation pair-once kernel
+    (threads=0: the default)."""
+    _check("pp_gravity_pairs_plan", lib().pp_gravity_pairs_plan(int(threads), int(R), int(super_log2)))
+
+
+def pp_gravity_pairs_get_plan(n):
+    """(threads, R, super_log2) pp_gravity_pairs uses for n bodies."""
+    t, r, lg = _I(), _I(), _I()
+    _check("pp_gravity_pairs_get_plan", lib().pp_gravity_pairs_get_plan(int(n), ctypes.byref(t),
+                                                                        ctypes.byref(r), ctypes.byref(lg)))
+    return int(t.value), int(r.value), int(lg.value)
 
 
 def pp_gravity_pairs_eligible(n, eps=0.01, flags=0):

@@ -73,6 +73,7 @@ class Simulation:
         self.state = nv.state_struct(t, n, ng, 0, self.grav_flags)
         self.ctx = None
         self.lanes = None
+        self.grid_shift = 0
         self.nb_per_particle = nb_per_particle
         self.batch = None
         if batch_offsets is not None:
@@ -91,6 +92,8 @@ class Simulation:
         self.ctx = nv.Ctx(max(1, self.n_gas), capacity, device=self.device, **self.params)
         if self.lanes:
             self.ctx.set_lanes(self.lanes)
+        if self.grid_shift:
+            self.ctx.set_grid_shift(self.grid_shift)
         if self.batch is not None:
             nv.sph_ctx_set_batch(self.ctx, self.batch)
         if old is not None:
@@ -205,6 +208,12 @@ class Simulation:
         g0, g1 = int(self.gas_off[s]), int(self.gas_off[s + 1])
         d0, d1 = int(self.dark_off[s]), int(self.dark_off[s + 1])
         return np.concatenate([np.arange(g0, g1), self.n_gas + np.arange(d0, d1)])
+
+    def set_grid_shift(self, shift):
+        """Octaves added to the finest cell size of the sort's derived grid."""
+        self.grid_shift = int(shift)
+        self.ctx.set_grid_shift(self.grid_shift)
+        self.graph = None
 
     def set_lanes(self, lanes):
         """Lanes per neighbour row in the density / force kernels."""

@@ -2,12 +2,15 @@
 
 Gravity has two kernels: the one-sided one, with two knobs (R targets per
 thread, S CTAs per cluster sharing the source range; the batched form has
-R), and the pair-once one, which wins once a launch has enough tiles to fill
-the GPU.  A built-in cost model and a measured default crossover choose
-without timing; these functions time the candidates instead and fix the
-fastest (sph_gravity_tune / sph_batch_set_plan / pp_gravity_pairs_min_n),
-returning the measurements.  tune_lanes does the same for the lanes per
-neighbour row of the SPH sums.
+R), and the pair-once one, with its block shape (threads per CTA, targets
+per thread: the j-tile width is the block) and super-tile side, which wins
+once a launch has enough tiles to fill the GPU.  A built-in cost model, a
+default plan and a measured default crossover choose without timing; these
+functions time the candidates instead and fix the fastest
+(sph_gravity_tune / sph_batch_set_plan / pp_gravity_pairs_plan /
+pp_gravity_pairs_min_n), returning the measurements.  tune_lanes does the
+same for the lanes per neighbour row of the SPH sums, tune_grid for the cell
+size of the neighbour search's grid.
 """
 from __future__ import annotations
 
@@ -110,3 +113,62 @@ def tune_pairs_threshold(make_pos_m, sizes=(8192, 12288, 16384, 24576, 32768, 49
         nv.pp_gravity_pairs_min_n(threshold)
     return threshold, res
 
+
+
+# pair-once plans: (threads per CTA, targets per thread), i.e. blocks of
+# 1024, 768, 1280 and 2048 bodies
+PAIRS_SHAPES = [(128, 8), (128, 6), (128, 10), (256, 8)]
+
+
+def tune_pairs_plan(pos_m, work, G=1.0, eps=0.01, shapes=None, super_offsets=(0, -1, 1), reps=2,
+                    apply=True):
+    """Time pp_gravity_pairs on pos_m for every block shape and super-tile
+    side (the size-chosen side plus the offsets); fix the fastest if apply
+    (else restore the default).  Returns ((threads, R, super_log2), {plan: ms})."""
+    out = torch.empty_like(pos_m)
+    n = pos_m.shape[0]
+    res = {}
+    try:
+        for threads, R in shapes or PAIRS_SHAPES:
+            nv.pp_gravity_pairs_plan(threads, R, -1)
+            _, _, lg0 = nv.pp_gravity_pairs_get_plan(n)
+            for off in super_offsets:
+                lg = lg0 + off
+                if lg < 0 or lg > 8:
+                    continue
+                nv.pp_gravity_pairs_plan(threads, R, lg)
+                res[(threads, R, lg)] = _time(lambda: nv.pp_gravity_pairs(pos_m, out, work, G, eps), reps)
+    finally:
+        nv.pp_gravity_pairs_plan(0)
+    best = min(res, key=res.get)
+    if apply:
+        nv.pp_gravity_pairs_plan(*best)
+    return best, res
+
+
+def tune_grid(sim, shifts=(-1, 0, 1), reps=3, apply=True):
+    """Time the sort and the neighbour-list build of a Simulation (at its
+    current working copies) for each octave shift of the derived grid's
+    finest cell; keep the fastest if apply (else restore the shift it had).
+    Returns (shift, {shift: ms})."""
+    if sim.n_gas == 0:
+        return 0, {}
+    t = sim.t
+    old = sim.grid_shift
+    res = {}
+
+    def build():
+        nv.sph_bin_and_sort(sim.ctx, t["pos_h"])
+        nv.sph_build_neighbors(sim.ctx, sim.n_gas, want_needed=False)
+    try:
+        for sh in shifts:
+            sim.set_grid_shift(sh)
+            res[sh] = _time(build, reps)
+    finally:
+        sim.set_grid_shift(old)
+    best = min(res, key=res.get)
+    if apply:
+        sim.set_grid_shift(best)
+    # leave the context's sort and lists as the step expects them
+    build()
+    return best, res
