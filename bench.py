@@ -556,11 +556,13 @@ def run_ensemble(args):
     best_R, tune = None, None
     if not pairs:
         best_R, tune = tune_batch(bsim.batch, bsim.t["pos_m"], reps=3)
-    # the SPH knobs of the batch: grid cell size and lanes per neighbour row
-    best_shift, tune_shift = tune_grid(bsim, reps=3)
-    best_lanes, tune_l = tune_lanes(bsim, reps=3)
     for _ in range(args.warmup):
         bsim.step(dt)
+    # the SPH knobs of the batch, tuned after the warm-up steps (the initial
+    # smoothing lengths give a few outlying rows with huge lists): grid cell
+    # size and lanes per neighbour row
+    best_shift, tune_shift = tune_grid(bsim, reps=3)
+    best_lanes, tune_l = tune_lanes(bsim, reps=3)
     bsim.capture(dt)
     launches0 = nv.sph_launch_count()
     ms_b = timed(lambda: bsim.replay(check=False), args.steps)
