@@ -647,10 +647,13 @@ def run_serve(args):
         req["k"] = k
     server = Server(int(args.serve_budget_gb * (1 << 30)), max_resident=args.max_resident,
                     n_streams=8)
+    server.set_policy(nv.SPH_SERVE_SHORTEST_FIRST if args.serve_policy == "sjf" else nv.SPH_SERVE_FIFO)
     jobs, steps, wall = replay_trace(server, trace, lambda req: made[req["k"]], args.serve_window)
     done = [j for j in jobs.values() if j["state"] == nv.SIM_DONE]
     lat = np.array([j["latency_s"] for j in done]) if done else np.zeros(0)
-    step_ms = np.array([x["ms"] for x in steps if x["resident"] or x["ms"] > 0])
+    # every simulation step's own latency (CUDA events on its stream)
+    step_ms = server.step_times()
+    call_ms = np.array([x["ms"] for x in steps if x["resident"] or x["ms"] > 0])
     served_ps = sum(j["steps_done"] * j["n"] for j in jobs.values())
     served_int = sum(j["steps_done"] * float(j["n"]) ** 2 for j in jobs.values())
     span = max(x["t"] for x in trace) - min(x["t"] for x in trace)
@@ -665,9 +668,13 @@ def run_serve(args):
                                "[4096, 1048576], steps U{10..1000}",
                    "jobs_in_trace": len(trace), "window_s": args.serve_window,
                    "budget_gb": args.serve_budget_gb, "max_resident": args.max_resident,
+                   "admission": args.serve_policy,
                    "input_prep_s": prep_s},
-        "step_latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "count": len(step_ms)},
-        "request_latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "completed": len(done)},
+        "step_latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "count": len(step_ms),
+                            "note": "each simulation step's own CUDA-event time on its stream"},
+        "server_call_ms": {"p50": pct(call_ms, 50), "p99": pct(call_ms, 99), "count": len(call_ms)},
+        "request_latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "completed": len(done),
+                              "completed_small": sum(1 for j in done if j["n"] < 131072)},
         "offered": {"particle_steps_per_s": offered_ps, "interactions_per_s": offered_int},
         "served": {"particle_steps_per_s": served_ps / wall, "interactions_per_s": served_int / wall},
         "submitted": len(jobs), "wall_s": wall,
@@ -825,6 +832,8 @@ def main(argv=None):
     ap.add_argument("--serve-window", type=float, default=90.0)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--max-resident", type=int, default=16)
+    ap.add_argument("--serve-policy", choices=["fifo", "sjf"], default="fifo",
+                    help="admission order of queued requests (sjf: least estimated work first)")
     ap.add_argument("--conservation", action="store_true",
                     help="report the energy and momentum change over the timed steps")
     ap.add_argument("--no-e2e", action="store_true")

@@ -517,7 +517,8 @@ typedef struct SimRequest {
 #define SIM_FAILED  3
 
 /* Status of one request.  Times are seconds of a monotonic host clock.  The
- * step latency percentiles are over the server steps the job took part in.
+ * step latency percentiles are over the job's own steps (CUDA events on its
+ * stream).
  * When state == SIM_DONE, h_r / h_v / h_e point to the final state (owned by
  * the server, valid until sim_release). */
 typedef struct SimStatus {
@@ -537,8 +538,11 @@ typedef struct sph_server sph_server;
 /* A server over a caller-allocated device arena of arena_bytes (256-byte
  * aligned): the memory budget.  Each admitted simulation takes its state
  * and context workspace from the arena (first fit) and gives them back when
- * it finishes.  At most max_resident simulations are advanced together, on
- * n_streams CUDA streams the server creates. */
+ * it finishes.  At most max_resident simulations are resident together, each
+ * on a CUDA stream of its own out of max(n_streams, max_resident) streams the
+ * server creates; half of them have the device's higher stream priority and
+ * take the jobs below 131,072 particles, so the GPU schedules a small job's
+ * thread blocks ahead of a large job's as SMs free up. */
 int sph_server_create(const SphParams *params, void *d_arena, size_t arena_bytes,
                       int32_t max_resident, int32_t n_streams, sph_server **out);
 int sph_server_destroy(sph_server *s);
@@ -547,13 +551,31 @@ int sph_server_destroy(sph_server *s);
  * arena; otherwise *job_id identifies it. */
 int sim_submit(sph_server *s, const SimRequest *req, uint64_t *job_id);
 
-/* One serving step: admit queued requests (first fit, FIFO order) while
- * memory and slots allow, launch one step of every resident simulation (the
- * initial RHS on its first), wait for them, retire the finished ones (final
- * state to host, memory back to the arena).  Returns the number still
- * resident and the wall time of the step in milliseconds (either may be
- * NULL). */
+/* One serving step (continuous batching, no lockstep): admit queued
+ * requests (first fit, in the policy's order) while memory and slots allow; collect
+ * every resident simulation's step that has finished (its CUDA event),
+ * retire the simulations that are done (final state to host, memory back to
+ * the arena) and launch the next step (the initial RHS on the first) of
+ * every simulation with nothing in flight.  If no step had finished, waits
+ * for the first that does.  So a small simulation takes many steps while a
+ * large one takes one.  Returns the number still resident and the wall time
+ * of the call in milliseconds (either may be NULL); SPH_ERR_TIMEOUT if no
+ * step finished within an hour. */
 int sph_server_step(sph_server *s, int32_t *h_resident, double *h_step_ms);
+
+/* Order in which queued requests are admitted: SPH_SERVE_FIFO (default,
+ * arrival order) or SPH_SERVE_SHORTEST_FIRST (least estimated GPU work left
+ * first: steps x (N^2 gravity + N SPH + per-step launches); under overload it
+ * completes the most requests and starves the largest). */
+#define SPH_SERVE_FIFO           0
+#define SPH_SERVE_SHORTEST_FIRST 1
+int sph_server_set_policy(sph_server *s, int32_t policy);
+
+/* Latencies (ms) of every simulation step the server has completed, in
+ * completion order: each from CUDA events on the simulation's stream around
+ * its own step (so they include time spent queued behind other jobs' work).
+ * Writes min(count, cap) of them to h_ms and the count to *h_count. */
+int sph_server_step_times(sph_server *s, float *h_ms, int32_t cap, int32_t *h_count);
 
 /* Status of a request (thread-safe); SPH_ERR_NOT_FOUND for an unknown id. */
 int sim_poll(sph_server *s, uint64_t job_id, SimStatus *out);

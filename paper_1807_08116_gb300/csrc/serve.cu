@@ -1,15 +1,23 @@
 // serve.cu -- the serving loop: simulations submitted as requests, admitted
-// against a device-memory budget, kept resident, advanced step by step
-// together (continuous batching: new requests are admitted between steps as
-// memory and slots free up), their final state copied back when done.
+// against a device-memory budget, kept resident and advanced step by step,
+// their final state copied back when done.
+//
+// Continuous batching without lockstep: every resident simulation has a
+// CUDA stream of its own, and a server step launches the next step of each
+// simulation whose previous step has finished (read from a CUDA event on its
+// stream), so a small job takes many steps while a large one takes one, and
+// requests that arrive are admitted between steps as memory and slots free
+// up.  Small jobs run on high-priority streams, whose thread blocks the GPU
+// schedules first as SMs free up.  A step's latency is its own CUDA-event
+// time on its stream, including any time its kernels queued behind other
+// jobs' work.
 //
 // Device memory comes from one caller-allocated arena (the budget) that the
 // server sub-allocates first-fit; each resident simulation owns its state
-// arrays and its context workspace inside the arena and runs on one stream of
-// a small pool, so the launches of different simulations overlap on the GPU.
-// Every computation is the same sequence of library calls a lone simulation
-// makes (sph_rhs_initial, sph_step), so a job's result does not depend on
-// what else is resident.
+// arrays and its context workspace inside the arena.  Every computation is
+// the same sequence of library calls a lone simulation makes
+// (sph_rhs_initial, sph_step), so a job's result does not depend on what else
+// is resident.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -17,6 +25,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -94,9 +103,15 @@ struct Job {
     sph_ctx *ctx = nullptr;
     long long capacity = 0;
     int log2_M = 10;
-    int stream_slot = 0;
+    int stream_slot = -1;         // the job's own stream while resident
     bool rhs_done = false;
+    bool in_flight = false;       // a launched step has not been harvested
+    bool step_in_launch = false;  // ... and it included a step (not the RHS alone)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the launched step
 };
+
+// Jobs below this many particles take the high-priority streams.
+constexpr int kSmallJob = 131072;
 
 // Scratch of the pair-once gravity kernel for jobs it applies to (0 if none).
 size_t pairs_bytes(const SphParams &p, int n) {
@@ -158,6 +173,10 @@ struct sph_server {
     Arena arena;
     int max_resident = 8;
     std::vector<cudaStream_t> streams;
+    std::vector<int> stream_busy;   // the resident job on each stream (1) or none (0)
+    int n_high = 0;                 // streams [0, n_high) have the higher priority
+    std::vector<float> step_ms_all; // latency of every step taken, in completion order
+    int policy = SPH_SERVE_FIFO;    // order in which queued requests are admitted
     std::map<uint64_t, Job> jobs;
     std::deque<uint64_t> queue;
     std::vector<uint64_t> resident;
@@ -173,8 +192,16 @@ namespace {
 // the host side after launching work), and the arena may hand the same bytes
 // to another job on another stream at once, so the stream is drained first.
 void free_device(sph_server *s, Job &j) {
-    if ((j.has_ws || j.has_state) && !s->streams.empty())
+    if (j.stream_slot >= 0 && (j.has_ws || j.has_state || j.in_flight))
         cudaStreamSynchronize(s->streams[j.stream_slot]);
+    if (j.ev0) cudaEventDestroy(j.ev0);
+    if (j.ev1) cudaEventDestroy(j.ev1);
+    j.ev0 = j.ev1 = nullptr;
+    j.in_flight = false;
+    if (j.stream_slot >= 0) {
+        s->stream_busy[j.stream_slot] = 0;
+        j.stream_slot = -1;
+    }
     if (j.ctx) {
         sph_ctx_destroy(j.ctx);
         j.ctx = nullptr;
@@ -268,26 +295,60 @@ int admit(sph_server *s, Job &j, cudaStream_t st) {
         free_device(s, j);
         return rc;
     }
+    if (cudaEventCreate(&j.ev0) != cudaSuccess || cudaEventCreate(&j.ev1) != cudaSuccess) {
+        free_device(s, j);
+        return SPH_ERR_CUDA;
+    }
     j.state = JOB_RUNNING;
     j.t_admit = now_s();
     return SPH_OK;
 }
 
+// A free stream for a job of n particles: a high-priority one for small jobs
+// (normal if none is free), a normal one for the others (high if none is).
+int pick_stream(sph_server *s, int n) {
+    const int ns = (int)s->streams.size();
+    const bool small = n < kSmallJob;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < ns; ++k) {
+            const bool high = k < s->n_high;
+            if (!s->stream_busy[k] && (pass == 1 || high == small)) return k;
+        }
+    return -1;
+}
+
+// Estimated seconds of GPU work a request still needs: its steps times the
+// cost of one (direct gravity ~ N^2 at ~3.9e12 pair terms per second, the SPH
+// stages ~ 4 ns per particle, ~0.5 ms of launches per step).
+double work_left(const Job &j) {
+    const double n = (double)j.n;
+    return (double)(j.n_steps - j.steps_done + 1) * (n * n / 3.9e12 + n * 4e-9 + 5e-4);
+}
+
 void admit_queued(sph_server *s) {
+    if (s->policy == SPH_SERVE_SHORTEST_FIRST)
+        std::stable_sort(s->queue.begin(), s->queue.end(), [&](uint64_t a, uint64_t b) {
+            return work_left(s->jobs[a]) < work_left(s->jobs[b]);
+        });
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->resident.size() < s->max_resident;) {
         Job &j = s->jobs[*it];
-        const int slot = (int)(j.id % s->streams.size());
+        const int slot = pick_stream(s, j.n);
+        if (slot < 0) break;   // every stream holds a resident job
         j.stream_slot = slot;
+        s->stream_busy[slot] = 1;
         int rc = admit(s, j, s->streams[slot]);
         if (rc == SPH_OK) {
             s->resident.push_back(j.id);
             it = s->queue.erase(it);
-        } else if (rc == SPH_ERR_BUDGET && !s->resident.empty()) {
-            ++it;   // does not fit now; smaller ones behind it may
-        } else {    // failed, or does not fit even into an empty arena
-            j.state = JOB_FAILED;
-            j.error = rc;
-            it = s->queue.erase(it);
+        } else {
+            free_device(s, j);   // whatever the failed admission holds, its stream included
+            if (rc == SPH_ERR_BUDGET && !s->resident.empty()) {
+                ++it;   // does not fit now; smaller ones behind it may
+            } else {    // failed, or does not fit even into an empty arena
+                j.state = JOB_FAILED;
+                j.error = rc;
+                it = s->queue.erase(it);
+            }
         }
     }
 }
@@ -305,15 +366,24 @@ extern "C" int sph_server_create(const SphParams *params, void *d_arena, size_t 
     s->arena_base = static_cast<char *>(d_arena);
     s->arena.init(arena_bytes);
     s->max_resident = max_resident;
-    for (int i = 0; i < n_streams; ++i) {
+    int lo = 0, hi = 0;   // numerically lower is the higher priority
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+        delete s;
+        return SPH_ERR_CUDA;
+    }
+    const int ns = std::max(n_streams, max_resident);
+    s->n_high = ns >= 2 ? ns / 2 : 0;
+    for (int i = 0; i < ns; ++i) {
         cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < s->n_high ? hi : lo) !=
+            cudaSuccess) {
             for (auto x : s->streams) cudaStreamDestroy(x);
             delete s;
             return SPH_ERR_CUDA;
         }
         s->streams.push_back(st);
     }
+    s->stream_busy.assign(ns, 0);
     *out = s;
     return SPH_OK;
 }
@@ -358,77 +428,158 @@ extern "C" int sim_submit(sph_server *s, const SimRequest *req, uint64_t *job_id
     return SPH_OK;
 }
 
-extern "C" int sph_server_step(sph_server *s, int32_t *h_resident, double *h_step_ms) {
-    if (!s) return SPH_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(s->mu);
-    admit_queued(s);
-    const double t0 = now_s();
-    // launch one step of every resident simulation, each on its stream
-    for (uint64_t id : s->resident) {
-        Job &j = s->jobs[id];
-        cudaStream_t st = s->streams[j.stream_slot];
-        int rc = SPH_OK;
-        if (!j.rhs_done) {
-            rc = sph_rhs_initial(j.ctx, &j.st, (sph_stream_t)st);
-            j.rhs_done = true;
-        }
-        if (rc == SPH_OK && j.steps_done < j.n_steps) rc = sph_step(j.ctx, &j.st, j.dt, (sph_stream_t)st);
-        if (rc) {
+namespace {
+
+// Launch the next step of resident job j on its stream (the initial RHS
+// first, on its first launch), between its two events.
+void launch_step(sph_server *s, Job &j) {
+    cudaStream_t st = s->streams[j.stream_slot];
+    int rc = SPH_OK;
+    if (cudaEventRecord(j.ev0, st) != cudaSuccess) rc = SPH_ERR_CUDA;
+    if (rc == SPH_OK && !j.rhs_done) {
+        rc = sph_rhs_initial(j.ctx, &j.st, (sph_stream_t)st);
+        j.rhs_done = true;
+    }
+    j.step_in_launch = rc == SPH_OK && j.steps_done < j.n_steps;
+    if (j.step_in_launch) rc = sph_step(j.ctx, &j.st, j.dt, (sph_stream_t)st);
+    if (rc == SPH_OK && cudaEventRecord(j.ev1, st) != cudaSuccess) rc = SPH_ERR_CUDA;
+    if (rc) {
+        j.state = JOB_FAILED;
+        j.error = rc;
+        return;
+    }
+    j.in_flight = true;
+}
+
+// Job j's launched step has finished: count it, check its device status and
+// list capacity (growing the context between steps), and copy the final
+// state back when the job is done.
+void harvest(sph_server *s, Job &j) {
+    cudaStream_t st = s->streams[j.stream_slot];
+    j.in_flight = false;
+    if (j.step_in_launch) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, j.ev0, j.ev1);
+        j.steps_done += 1;
+        j.step_ms.push_back(ms);
+        s->step_ms_all.push_back(ms);
+    }
+    if (j.state == JOB_RUNNING && j.n_gas > 0) {
+        int32_t flags = 0;
+        int rc = sph_ctx_device_status(j.ctx, (sph_stream_t)st, &flags);
+        if (flags & SPH_FLAG_NB_OVERFLOW) {
+            j.state = JOB_FAILED;
+            j.error = SPH_ERR_NB_OVERFLOW;
+        } else if (rc != SPH_OK && rc != SPH_ERR_DEVICE) {
             j.state = JOB_FAILED;
             j.error = rc;
-        }
-    }
-    for (auto st : s->streams)
-        if (cudaStreamSynchronize(st) != cudaSuccess) return SPH_ERR_CUDA;
-    const double ms = (now_s() - t0) * 1e3;
-    std::vector<uint64_t> still;
-    for (uint64_t id : s->resident) {
-        Job &j = s->jobs[id];
-        cudaStream_t st = s->streams[j.stream_slot];
-        if (j.state == JOB_RUNNING && j.steps_done < j.n_steps) {
-            j.steps_done += 1;
-            j.step_ms.push_back((float)ms);
-        }
-        if (j.state == JOB_RUNNING && j.n_gas > 0) {
-            int32_t flags = 0;
-            int rc = sph_ctx_device_status(j.ctx, (sph_stream_t)st, &flags);
-            if (flags & SPH_FLAG_NB_OVERFLOW) {
-                j.state = JOB_FAILED;
-                j.error = SPH_ERR_NB_OVERFLOW;
-            } else if (rc != SPH_OK && rc != SPH_ERR_DEVICE) {
-                j.state = JOB_FAILED;
-                j.error = rc;
-            } else if (j.steps_done < j.n_steps) {
-                int64_t used = 0;
-                if (sph_ctx_nb_total(j.ctx, (sph_stream_t)st, &used) == SPH_OK &&
-                    used > 0.7 * (double)j.capacity) {
-                    // grow between steps: re-sort the same working copies into
-                    // a larger context (the lists are a function of pos_h)
-                    int rc2 = make_ctx(s, j, (long long)(used * 1.6) + 1024, st);
-                    if (rc2 == SPH_OK) rc2 = size_lists(s, j, st);
-                    if (rc2 != SPH_OK) {
-                        j.state = JOB_FAILED;
-                        j.error = rc2;
-                    }
+        } else if (j.steps_done < j.n_steps) {
+            int64_t used = 0;
+            if (sph_ctx_nb_total(j.ctx, (sph_stream_t)st, &used) == SPH_OK &&
+                used > 0.7 * (double)j.capacity) {
+                // grow between steps: re-sort the same working copies into
+                // a larger context (the lists are a function of pos_h)
+                int rc2 = make_ctx(s, j, (long long)(used * 1.6) + 1024, st);
+                if (rc2 == SPH_OK) rc2 = size_lists(s, j, st);
+                if (rc2 != SPH_OK) {
+                    j.state = JOB_FAILED;
+                    j.error = rc2;
                 }
             }
         }
-        if (j.state == JOB_RUNNING && j.steps_done >= j.n_steps) {
-            const size_t n = j.n, ng = j.n_gas;
-            bool ok = cudaMemcpyAsync(j.r.data(), j.st.r, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                      cudaMemcpyAsync(j.v.data(), j.st.v, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                      (ng == 0 || cudaMemcpyAsync(j.e.data(), j.st.e, ng * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess) &&
-                      cudaStreamSynchronize(st) == cudaSuccess;
-            j.state = ok ? JOB_DONE : JOB_FAILED;
-            if (!ok) j.error = SPH_ERR_CUDA;
-            j.t_done = now_s();
-        }
-        if (j.state == JOB_RUNNING) still.push_back(id);
-        else free_device(s, j);
     }
-    s->resident.swap(still);
+    if (j.state == JOB_RUNNING && j.steps_done >= j.n_steps) {
+        const size_t n = j.n, ng = j.n_gas;
+        bool ok = cudaMemcpyAsync(j.r.data(), j.st.r, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  cudaMemcpyAsync(j.v.data(), j.st.v, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  (ng == 0 || cudaMemcpyAsync(j.e.data(), j.st.e, ng * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess) &&
+                  cudaStreamSynchronize(st) == cudaSuccess;
+        j.state = ok ? JOB_DONE : JOB_FAILED;
+        if (!ok) j.error = SPH_ERR_CUDA;
+        j.t_done = now_s();
+    }
+}
+
+}  // namespace
+
+extern "C" int sph_server_step(sph_server *s, int32_t *h_resident, double *h_step_ms) {
+    if (!s) return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    const double t0 = now_s();
+    admit_queued(s);
+    bool progressed = false;
+    for (int pass = 0; pass < 2; ++pass) {
+        // harvest the steps that have finished
+        for (uint64_t id : s->resident) {
+            Job &j = s->jobs[id];
+            if (!j.in_flight) continue;
+            const cudaError_t q = cudaEventQuery(j.ev1);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                j.state = JOB_FAILED;
+                j.error = SPH_ERR_CUDA;
+                j.in_flight = false;
+                continue;
+            }
+            harvest(s, j);
+            progressed = true;
+        }
+        // retire the jobs that finished or failed, then launch the next step
+        // of every idle resident job
+        std::vector<uint64_t> still;
+        for (uint64_t id : s->resident) {
+            Job &j = s->jobs[id];
+            if (j.state == JOB_RUNNING) still.push_back(id);
+            else free_device(s, j);
+        }
+        s->resident.swap(still);
+        for (uint64_t id : s->resident) {
+            Job &j = s->jobs[id];
+            if (!j.in_flight) launch_step(s, j);
+        }
+        bool any = false;
+        for (uint64_t id : s->resident) any |= s->jobs[id].in_flight;
+        if (progressed || !any) break;
+        // nothing finished yet: wait for the first step that does (bounded)
+        const double tw = now_s();
+        bool done = false;
+        while (!done) {
+            for (uint64_t id : s->resident) {
+                const Job &j = s->jobs[id];
+                if (j.in_flight && cudaEventQuery(j.ev1) != cudaErrorNotReady) done = true;
+            }
+            if (!done) {
+                if (now_s() - tw > 3600.0) return SPH_ERR_TIMEOUT;
+                std::this_thread::sleep_for(std::chrono::microseconds(50));
+            }
+        }
+    }
+    // memory and slots freed by retired jobs take queued requests at once
+    admit_queued(s);
+    for (uint64_t id : s->resident) {
+        Job &j = s->jobs[id];
+        if (!j.in_flight && j.state == JOB_RUNNING) launch_step(s, j);
+    }
     if (h_resident) *h_resident = (int32_t)s->resident.size();
-    if (h_step_ms) *h_step_ms = ms;
+    if (h_step_ms) *h_step_ms = (now_s() - t0) * 1e3;
+    return SPH_OK;
+}
+
+extern "C" int sph_server_set_policy(sph_server *s, int32_t policy) {
+    if (!s || (policy != SPH_SERVE_FIFO && policy != SPH_SERVE_SHORTEST_FIRST))
+        return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->policy = policy;
+    return SPH_OK;
+}
+
+extern "C" int sph_server_step_times(sph_server *s, float *h_ms, int32_t cap, int32_t *h_count) {
+    if (!s || !h_count || cap < 0 || (cap > 0 && !h_ms)) return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    const int32_t n = (int32_t)s->step_ms_all.size();
+    *h_count = n;
+    if (cap > 0 && n > 0)
+        std::memcpy(h_ms, s->step_ms_all.data(), sizeof(float) * (size_t)std::min(n, cap));
     return SPH_OK;
 }
 

@@ -36,6 +36,7 @@ SPH_GRAV_POTENTIAL = 1
 SPH_GRAV_NO_KAHAN = 2
 
 SPH_PREDICT, SPH_CORRECT, SPH_EMIT = 0, 1, 2
+SPH_SERVE_FIFO, SPH_SERVE_SHORTEST_FIRST = 0, 1
 
 _ERR_NAMES = {1: "INVALID_ARG", 2: "CUDA_ERROR", 3: "NB_OVERFLOW", 4: "BUDGET", 5: "TIMEOUT",
               6: "NOT_FOUND", 7: "DEVICE_ERROR"}
@@ -170,6 +171,8 @@ def lib():
             "sim_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(SimStatus)]),
             "sim_release": (_I, [_P, ctypes.c_uint64]),
             "sph_server_info": (_I, [_P, ctypes.POINTER(SphServerInfo)]),
+            "sph_server_step_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
+            "sph_server_set_policy": (_I, [_P, _I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

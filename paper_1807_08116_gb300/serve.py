@@ -1,5 +1,6 @@
 """Serving: a thin Python face of the library's request server (sim_submit,
-sph_server_step, sim_poll) and a driver that replays a timed request trace.
+sph_server_step, sim_poll, sph_server_step_times) and a driver that replays
+a timed request trace.
 
 All scheduling, admission against the memory budget and stepping happen in
 the C++ server (csrc/serve.cu); this module marshals arrays and keeps time.
@@ -61,6 +62,20 @@ class Server:
             out["v"] = arr(st.h_v, 3 * n).reshape(3, n).T
             out["e"] = arr(st.h_e, ng) if ng else np.zeros(0)
         return out
+
+    def set_policy(self, policy):
+        """nv.SPH_SERVE_FIFO or nv.SPH_SERVE_SHORTEST_FIRST admission order."""
+        nv._check("sph_server_set_policy", nv.lib().sph_server_set_policy(self.handle, int(policy)))
+
+    def step_times(self):
+        """Latencies (ms) of every simulation step completed so far."""
+        cnt = ctypes.c_int32()
+        nv._check("sph_server_step_times", nv.lib().sph_server_step_times(self.handle, None, 0,
+                                                                          ctypes.byref(cnt)))
+        buf = np.zeros(max(cnt.value, 1), np.float32)
+        nv._check("sph_server_step_times", nv.lib().sph_server_step_times(
+            self.handle, buf.ctypes.data_as(ctypes.c_void_p), buf.size, ctypes.byref(cnt)))
+        return buf[:min(cnt.value, buf.size)].copy()
 
     def release(self, jid):
         nv._check("sim_release", nv.lib().sim_release(self.handle, int(jid)))

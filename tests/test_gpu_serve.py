@@ -168,3 +168,56 @@ def test_admission_that_fails_after_sizing_lists_leaves_the_next_job_intact(orc)
     for k in ("r", "v", "e"):
         assert np.array_equal(got[k], ref[k]), k
     assert srv.info()["arena_free_bytes"] == srv.info()["arena_bytes"]
+
+
+def test_small_job_is_not_held_to_the_pace_of_a_large_one():
+    # No lockstep: a small job with twice the steps of a large resident one
+    # finishes first, each step timed on its own stream, and its result is
+    # still exactly its lone result.
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server
+    big = ics.two_halo(65536, 65536, seed=52)
+    small = ics.single_halo(2048, 2048, seed=53)
+    alone = Server(2 << 30, max_resident=2, n_streams=2)
+    js = alone.submit(small, 16)
+    _run_all(alone)
+    ref = alone.poll(js, with_result=True)
+    srv = Server(4 << 30, max_resident=4, n_streams=4)
+    jb = srv.submit(big, 8)
+    js = srv.submit(small, 16)
+    for _ in range(100000):
+        srv.step()
+        if srv.poll(js)["state"] == nv.SIM_DONE:
+            break
+    sb = srv.poll(jb)
+    assert sb["steps_done"] < sb["n_steps"], sb     # the large job is still running
+    got = srv.poll(js, with_result=True)
+    for k in ("r", "v", "e"):
+        assert np.array_equal(got[k], ref[k]), k
+    _run_all(srv)
+    assert srv.poll(jb)["state"] == nv.SIM_DONE
+    times = srv.step_times()
+    assert len(times) == 8 + 16 and np.all(times > 0)
+    print(f"step ms: small p50 {got['step_ms_p50']:.2f}, large p50 {srv.poll(jb)['step_ms_p50']:.2f}")
+    assert got["step_ms_p50"] < srv.poll(jb)["step_ms_p50"]
+
+
+def test_shortest_first_admission():
+    # one slot: under FIFO the first request is admitted first; under
+    # shortest-first the request with the least work left is, whatever its
+    # place in the queue
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server
+    big = ics.two_halo(8192, 8192, seed=54)
+    small = ics.single_halo(1024, 1024, seed=55)
+    for policy, first in ((nv.SPH_SERVE_FIFO, "big"), (nv.SPH_SERVE_SHORTEST_FIRST, "small")):
+        srv = Server(1 << 30, max_resident=1, n_streams=1)
+        srv.set_policy(policy)
+        ids = {"big": srv.submit(big, 3), "small": srv.submit(small, 3)}
+        _run_all(srv)
+        st = {k: srv.poll(v) for k, v in ids.items()}
+        assert all(x["state"] == nv.SIM_DONE for x in st.values())
+        other = "small" if first == "big" else "big"
+        assert st[first]["done_s"] <= st[other]["admit_s"], (policy, st)
