@@ -141,9 +141,12 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->red = cv.take<unsigned>(8);
     c->red_fused = cv.take<unsigned>(8);
     c->flags = cv.take<int>(4);
+    // the scan's block totals, also the chunk totals of the one-launch sort,
+    // whose grid they cap: room for a full resident grid (a few blocks per SM)
     size_t nb_scan = (size_t)scan_block_count((long long)(M > n ? M : n));
-    c->block_sums = cv.take<int>(nb_scan + 32);
-    c->block_sums_cap = (int)(nb_scan + 32);
+    const size_t n_sums = std::max<size_t>(nb_scan + 32, 4096);
+    c->block_sums = cv.take<int>(n_sums);
+    c->block_sums_cap = (int)n_sums;
     c->pos_h_s = cv.take<float4>(n);
     c->vel_s = cv.take<float4>(n);
     c->aux_s = cv.take<float4>(n);
