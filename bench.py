@@ -683,6 +683,51 @@ def run_serve(args):
     return 0
 
 
+def run_sort(args):
+    """The sorting stage alone on the gas of the two-halo construction with
+    --n particles (half gas): sph_bin_and_sort as one cooperative launch and
+    as its kernel sequence, --warmup untimed and --steps timed sorts each,
+    CUDA events; the results of the two forms are bitwise equal (tested)."""
+    import torch
+
+    from paper_1807_08116_gb300 import ics
+    from paper_1807_08116_gb300 import native as nv
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nv.lib()
+    q = args.n // 4
+    d = ics.two_halo(q, q, seed=2)
+    ng = d["n_gas"]
+    ph = np.empty((ng, 4), np.float32)
+    ph[:, :3] = d["r"][:ng]
+    ph[:, 3] = d["h"]
+    x = torch.as_tensor(ph, device="cuda")
+    ctx = nv.Ctx(ng, 1024)
+    res = {}
+    for fused in (0, 1):
+        ctx.set_sort_fused(fused)
+        for _ in range(args.warmup):
+            nv.sph_bin_and_sort(ctx, x)
+        torch.cuda.synchronize()
+        l0 = nv.sph_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            nv.sph_bin_and_sort(ctx, x)
+        e1.record()
+        torch.cuda.synchronize()
+        res[fused] = (e0.elapsed_time(e1) / args.steps, (nv.sph_launch_count() - l0) / args.steps)
+    peak, note = hbm_peak()
+    byts = STAGE_BYTES["sp"][1] * ng
+    print(json.dumps({"metric": "sort stage ms", "n_gas": ng, "steps": args.steps, "warmup": args.warmup,
+                      "one_launch_ms": res[1][0], "sequence_ms": res[0][0],
+                      "kernels_per_sort": {"one_launch": res[1][1], "sequence": res[0][1]},
+                      "gbs_one_launch": byts / (res[1][0] / 1e3) / 1e9,
+                      "frac_of_hbm": byts / (res[1][0] / 1e3) / 1e9 / peak, "peak_note": note}),
+          flush=True)
+    return 0
+
+
 def run_gravity_sharded(args):
     """Gravity over --n particles split across the ranks by the paper's
     particle partition (Sect. 3): per launch, one all-gather of (x, y, z, m)
@@ -817,9 +862,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "gravity"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "gravity", "sort"],
                     default="large")
-    ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity")
+    ap.add_argument("--n", type=int, default=4194304, help="particles of --workload gravity / sort")
     ap.add_argument("--one-sided", action="store_true",
                     help="--workload gravity: time the one-sided kernel instead of the pair-once one")
     ap.add_argument("--tune", action="store_true",
@@ -857,6 +902,8 @@ def main(argv=None):
         return run_serve(args)
     if args.workload == "gravity":
         return run_gravity(args)
+    if args.workload == "sort":
+        return run_sort(args)
     return run_ours(args)
 
 
