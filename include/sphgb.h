@@ -580,6 +580,18 @@ int sph_server_step_times(sph_server *s, float *h_ms, int32_t cap, int32_t *h_co
 /* Status of a request (thread-safe); SPH_ERR_NOT_FOUND for an unknown id. */
 int sim_poll(sph_server *s, uint64_t job_id, SimStatus *out);
 
+/* Checkpoint of a resident request (thread-safe): waits for its step in
+ * flight (counting it), then copies its state to caller-owned host arrays:
+ * h_r[3n], h_v[3n] FP64 SoA, h_e[n_gas] FP64, and h_h[n_gas] the smoothing
+ * lengths its last evaluation used; *h_steps_done the steps taken.  The job
+ * keeps running.  Submitting the checkpoint as a new request (same masses,
+ * dt, and n_steps minus the steps taken) resumes it: the first evaluation
+ * of the new request recomputes exactly the right-hand side the job would
+ * have used next, so the resumed run is bitwise the uninterrupted one.
+ * SPH_ERR_INVALID_ARG if the job is not resident or has not started. */
+int sim_checkpoint(sph_server *s, uint64_t job_id, double *h_r, double *h_v, double *h_e,
+                   float *h_h, int32_t *h_steps_done);
+
 /* Forget a finished, failed or still-queued request and its results. */
 int sim_release(sph_server *s, uint64_t job_id);
 

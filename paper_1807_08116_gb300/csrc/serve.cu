@@ -613,6 +613,46 @@ extern "C" int sim_poll(sph_server *s, uint64_t job_id, SimStatus *out) {
     return SPH_OK;
 }
 
+extern "C" int sim_checkpoint(sph_server *s, uint64_t job_id, double *h_r, double *h_v, double *h_e,
+                              float *h_h, int32_t *h_steps_done) {
+    if (!s || !h_r || !h_v || !h_steps_done) return SPH_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return SPH_ERR_NOT_FOUND;
+    Job &j = it->second;
+    if (j.n_gas > 0 && (!h_e || !h_h)) return SPH_ERR_INVALID_ARG;
+    if (j.state != JOB_RUNNING || !j.rhs_done) return SPH_ERR_INVALID_ARG;
+    cudaStream_t st = s->streams[j.stream_slot];
+    if (j.in_flight) {
+        // let the launched step finish and count it, as a server step would
+        SPH_CUDA_TRY(cudaEventSynchronize(j.ev1));
+        harvest(s, j);
+        if (j.state == JOB_DONE) {   // that was its last step: the final state
+            std::memcpy(h_r, j.r.data(), sizeof(double) * 3 * (size_t)j.n);
+            std::memcpy(h_v, j.v.data(), sizeof(double) * 3 * (size_t)j.n);
+            if (j.n_gas) std::memcpy(h_e, j.e.data(), sizeof(double) * (size_t)j.n_gas);
+        }
+        if (j.state == JOB_FAILED) return j.error ? j.error : SPH_ERR_CUDA;
+    }
+    const size_t n = j.n, ng = j.n_gas;
+    if (j.state == JOB_RUNNING) {
+        SPH_CUDA_TRY(cudaMemcpyAsync(h_r, j.st.r, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        SPH_CUDA_TRY(cudaMemcpyAsync(h_v, j.st.v, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (ng) SPH_CUDA_TRY(cudaMemcpyAsync(h_e, j.st.e, ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (ng) {
+        // the smoothing length of the last evaluation: the h of the FP32
+        // working copy (x, y, z, h) its sort and density read
+        std::vector<float> ph(4 * ng);
+        SPH_CUDA_TRY(cudaMemcpyAsync(ph.data(), j.st.pos_h, 16 * ng, cudaMemcpyDeviceToHost, st));
+        SPH_CUDA_TRY(cudaStreamSynchronize(st));
+        for (size_t q = 0; q < ng; ++q) h_h[q] = ph[4 * q + 3];
+    }
+    SPH_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_steps_done = j.steps_done;
+    return SPH_OK;
+}
+
 extern "C" int sim_release(sph_server *s, uint64_t job_id) {
     if (!s) return SPH_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(s->mu);

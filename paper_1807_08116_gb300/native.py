@@ -173,6 +173,7 @@ def lib():
             "sph_server_info": (_I, [_P, ctypes.POINTER(SphServerInfo)]),
             "sph_server_step_times": (_I, [_P, _P, _I, ctypes.POINTER(_I)]),
             "sph_server_set_policy": (_I, [_P, _I]),
+            "sim_checkpoint": (_I, [_P, ctypes.c_uint64, _P, _P, _P, _P, ctypes.POINTER(_I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -77,6 +77,22 @@ class Server:
             self.handle, buf.ctypes.data_as(ctypes.c_void_p), buf.size, ctypes.byref(cnt)))
         return buf[:min(cnt.value, buf.size)].copy()
 
+    def checkpoint(self, jid):
+        """State of a resident job as an initial condition (r, v, e, h, m) and
+        the steps it has taken; submit it with the remaining steps to resume."""
+        st = self.poll(jid)
+        n, ng = st["n"], st["n_gas"]
+        r = np.empty(3 * n)
+        v = np.empty(3 * n)
+        e = np.empty(max(ng, 1))
+        h = np.empty(max(ng, 1), np.float32)
+        done = ctypes.c_int32()
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        nv._check("sim_checkpoint", nv.lib().sim_checkpoint(self.handle, int(jid), P(r), P(v), P(e), P(h),
+                                                            ctypes.byref(done)))
+        return dict(r=r.reshape(3, n).T.copy(), v=v.reshape(3, n).T.copy(), e=e[:ng].copy(),
+                    h=h[:ng].copy(), n=n, n_gas=ng), int(done.value)
+
     def release(self, jid):
         nv._check("sim_release", nv.lib().sim_release(self.handle, int(jid)))
 

@@ -221,3 +221,30 @@ def test_shortest_first_admission():
         assert all(x["state"] == nv.SIM_DONE for x in st.values())
         other = "small" if first == "big" else "big"
         assert st[first]["done_s"] <= st[other]["admit_s"], (policy, st)
+
+
+def test_checkpoint_resumes_bitwise():
+    # a checkpoint of a running job, submitted as a new request with the
+    # remaining steps, ends in exactly the state of the uninterrupted job
+    need_gpu()
+    from paper_1807_08116_gb300 import native as nv
+    from paper_1807_08116_gb300.serve import Server
+    d = ics.two_halo(1200, 800, seed=56)
+    total = 9
+    srv = Server(1 << 30, max_resident=2, n_streams=2)
+    j = srv.submit(d, total)
+    while srv.poll(j)["steps_done"] < 4:
+        srv.step()
+    ck, done = srv.checkpoint(j)
+    assert 4 <= done < total
+    _run_all(srv)
+    full = srv.poll(j, with_result=True)
+    ic = dict(ck)
+    ic["m"] = d["m"]
+    srv2 = Server(1 << 30, max_resident=2, n_streams=2)
+    j2 = srv2.submit(ic, total - done)
+    _run_all(srv2)
+    res = srv2.poll(j2, with_result=True)
+    assert res["state"] == nv.SIM_DONE
+    for k in ("r", "v", "e"):
+        assert np.array_equal(res[k], full[k]), k
