@@ -549,7 +549,7 @@ def run_ensemble(args):
         return e0.elapsed_time(e1)
 
     # (a) batched
-    from paper_1807_08116_gb300.tune import tune_batch, tune_grid, tune_lanes
+    from paper_1807_08116_gb300.tune import tune_batch, tune_batch_pairs_plan, tune_grid, tune_lanes
     bsim = Simulation(ic, batch_offsets=(go, do, so))
     bsim.initial_rhs()
     pairs = "grav_work" in bsim.t   # pair-once gravity over all simulations' tiles
@@ -563,6 +563,11 @@ def run_ensemble(args):
     # size and lanes per neighbour row
     best_shift, tune_shift = tune_grid(bsim, reps=3)
     best_lanes, tune_l = tune_lanes(bsim, reps=3)
+    best_plan, tune_plan = None, None
+    if pairs:   # the block shape of the pair-once launch over all simulations' tiles
+        best_plan, tune_plan = tune_batch_pairs_plan(bsim.batch, bsim.t["pos_m"], bsim.t["grav_work"],
+                                                     reps=2)
+        tune_plan = {str(list(k)): v for k, v in tune_plan.items()}
     bsim.capture(dt)
     launches0 = nv.sph_launch_count()
     ms_b = timed(lambda: bsim.replay(check=False), args.steps)
@@ -613,7 +618,9 @@ def run_ensemble(args):
                                else "one-sided persistent work queue"),
                    "gravity_units_R": best_R, "autotune_ms": tune,
                    "tuned": {"grid_shift": best_shift, "grid_shift_ms": tune_shift,
-                             "lanes": best_lanes, "lanes_ms": tune_l}},
+                             "lanes": best_lanes, "lanes_ms": tune_l,
+                             "pairs_plan": list(best_plan) if best_plan else None,
+                             "pairs_plan_ms": tune_plan}},
         "max_rel_position_diff_batched_vs_sequential": worst,
         "stage_ms_batched": stage_b,
         "interactions_per_step": float(sum(d["n"] ** 2 for d in lst)),

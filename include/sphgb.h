@@ -310,7 +310,8 @@ int pp_gravity_pairs(const float *d_pos_m, int32_t n, float G, float eps, float 
  * side (0..8; -1: chosen by size).  threads = 0 restores the default (128, 8,
  * -1).  Results of different plans agree to force rounding (other block
  * boundaries, so another summation order); one plan is bitwise reproducible.
- * Batches (pp_gravity_pairs_batched) always use the default shape. */
+ * Batches (pp_gravity_pairs_batched) take the plan's block shape too (the
+ * super-tile side does not apply to them). */
 int pp_gravity_pairs_plan(int32_t threads, int32_t R, int32_t super_log2_side);
 
 /* The plan pp_gravity_pairs uses for n bodies: threads per CTA, targets per

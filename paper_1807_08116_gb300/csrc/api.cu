@@ -103,8 +103,10 @@ struct sph_batch {
     int *d_counter;
     size_t units_cap;
     const int *d_sim_of_gas;
-    long long *d_tile_off;       // pair-once gravity: first tile of each simulation [n_sims + 1]
-    long long n_pair_tiles;
+    // pair-once gravity: first tile of each simulation [n_sims + 1] and the
+    // tile count, for each block shape a plan may name
+    long long *d_tile_off[kPairsNumShapes];
+    long long n_pair_tiles[kPairsNumShapes];
     void *d_pair_scales;         // pair-once gravity: fixed-point scale of each simulation
 };
 
@@ -731,7 +733,7 @@ BatchCarve batch_carve(int n_sims, size_t units_cap) {
     c.units = up(sizeof(int4) * (size_t)n_sims);
     c.counter = c.units + up(sizeof(int2) * units_cap);
     c.tile_off = c.counter + 256;
-    c.scales = c.tile_off + up(sizeof(long long) * ((size_t)n_sims + 1));
+    c.scales = c.tile_off + kPairsNumShapes * up(sizeof(long long) * ((size_t)n_sims + 1));
     c.total = c.scales + up(pairs_scale_bytes() * (size_t)n_sims);
     return c;
 }
@@ -792,19 +794,27 @@ extern "C" int sph_batch_create(int32_t n_sims, const int32_t *h_gas_off, const 
     b->d_counter = reinterpret_cast<int *>(base + c.counter);
     b->units_cap = cap;
     b->d_sim_of_gas = d_sim_of_gas;
-    b->d_tile_off = reinterpret_cast<long long *>(base + c.tile_off);
+    const size_t off_stride = (sizeof(long long) * ((size_t)n_sims + 1) + 255) & ~size_t(255);
+    for (int k = 0; k < kPairsNumShapes; ++k)
+        b->d_tile_off[k] = reinterpret_cast<long long *>(base + c.tile_off + k * off_stride);
     b->d_pair_scales = base + c.scales;
-    std::vector<long long> tile_off(n_sims + 1, 0);
-    for (int s = 0; s < n_sims; ++s)
-        tile_off[s + 1] = tile_off[s] + pairs_tiles((long long)b->h_sims[s].y + b->h_sims[s].w);
-    b->n_pair_tiles = tile_off[n_sims];
+    std::vector<long long> tile_off[kPairsNumShapes];
+    for (int k = 0; k < kPairsNumShapes; ++k) {
+        tile_off[k].assign(n_sims + 1, 0);
+        for (int s = 0; s < n_sims; ++s)
+            tile_off[k][s + 1] = tile_off[k][s] + pairs_tiles((long long)b->h_sims[s].y + b->h_sims[s].w,
+                                                              pairs_shape_block(k));
+        b->n_pair_tiles[k] = tile_off[k][n_sims];
+    }
     cudaStream_t st = (cudaStream_t)stream;
     int rc = SPH_OK;
     if (cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(int4) * n_sims, cudaMemcpyHostToDevice,
-                        st) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_tile_off, tile_off.data(), sizeof(long long) * (n_sims + 1),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+                        st) != cudaSuccess)
         rc = SPH_ERR_CUDA;
+    for (int k = 0; k < kPairsNumShapes && rc == SPH_OK; ++k)
+        if (cudaMemcpyAsync(b->d_tile_off[k], tile_off[k].data(), sizeof(long long) * (n_sims + 1),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = SPH_ERR_CUDA;
     if (rc == SPH_OK) rc = batch_build_units(b, 4, st);
     if (rc == SPH_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SPH_ERR_CUDA;
     if (rc != SPH_OK) {
@@ -844,15 +854,16 @@ extern "C" int pp_gravity_pairs_batched(const sph_batch *b, const float *d_pos_m
                                         size_t work_bytes, sph_stream_t stream) {
     if (!b || !(eps >= 0.0f) || !(G == G)) return SPH_ERR_INVALID_ARG;
     if (b->n == 0) return SPH_OK;
+    const int shape = pairs_current_shape();
     if (!pp_gravity_pairs_eligible(b->n, eps, flags) || !d_work ||
-        work_bytes < pp_gravity_pairs_workspace_bytes(b->n) || b->n_pair_tiles > 0x7fffffffll)
+        work_bytes < pp_gravity_pairs_workspace_bytes(b->n) || b->n_pair_tiles[shape] > 0x7fffffffll)
         return pp_gravity_batched(b, d_pos_m, G, eps, d_acc_pot, flags, stream);
     if (!d_pos_m || !d_acc_pot || !aligned16(d_pos_m) || !aligned16(d_acc_pot) ||
         (reinterpret_cast<uintptr_t>(d_work) & 255u))
         return SPH_ERR_INVALID_ARG;
     return launch_gravity_pairs_batched(reinterpret_cast<const float4 *>(d_pos_m), b->n, b->n_gas,
-                                        b->d_sims, b->d_tile_off, b->n_sims, b->n_pair_tiles,
-                                        b->d_pair_scales, G, eps,
+                                        b->d_sims, b->d_tile_off[shape], b->n_sims,
+                                        b->n_pair_tiles[shape], shape, b->d_pair_scales, G, eps,
                                         reinterpret_cast<float4 *>(d_acc_pot), flags, d_work,
                                         (cudaStream_t)stream);
 }

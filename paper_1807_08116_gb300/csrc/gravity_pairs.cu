@@ -71,8 +71,8 @@ struct PairsShape {
     static_assert(kB % GP_SLAB == 0 && GP_SLAB % 32 == 0, "slab shape");
 };
 
-// The default shape (128 threads, 8 targets each, blocks of 1024), which a
-// batch always uses; a single simulation takes the plan of pp_gravity_pairs_plan.
+// The default shape (128 threads, 8 targets each, blocks of 1024); both a
+// single simulation and a batch take the shape of pp_gravity_pairs_plan.
 constexpr int GP_THREADS = 128;
 constexpr int GP_RP = 4;
 constexpr int GP_B = PairsShape<GP_THREADS, GP_RP>::kB;
@@ -488,7 +488,7 @@ static PairsVariant pairs_pick(int threads, int rp, bool pot, bool batch) {
 }
 
 static void pairs_init() {
-    const int shapes[4][2] = {{128, 3}, {128, 4}, {128, 5}, {256, 4}};
+    const int shapes[kPairsNumShapes][2] = {{128, 3}, {128, 4}, {128, 5}, {256, 4}};
     for (auto &sh : shapes)
         for (int f = 0; f < 4; ++f) {
             const PairsVariant v = pairs_pick(sh[0], sh[1], f & 1, f & 2);
@@ -547,20 +547,33 @@ static int pairs_launch(const float4 *pos, int n, int n_gas, float G, float eps,
 
 size_t pairs_scale_bytes() { return sizeof(PairsScale); }
 
-// Tiles of simulation s with ns bodies in a batch (default shape):
-// nb_s (nb_s + 1) / 2, nb_s = ceil(ns / 1024).
-long long pairs_tiles(long long ns) {
-    const long long nb = (ns + GP_B - 1) / GP_B;
+// The block shapes a plan may name, in a fixed order (index 0..3).
+static const int kPairsShapes[kPairsNumShapes][2] = {{128, 3}, {128, 4}, {128, 5}, {256, 4}};
+
+int pairs_shape_block(int shape) { return kPairsShapes[shape][0] * 2 * kPairsShapes[shape][1]; }
+
+int pairs_current_shape() {
+    const PairsPlan p = pairs_plan();
+    for (int k = 0; k < kPairsNumShapes; ++k)
+        if (kPairsShapes[k][0] == p.threads && kPairsShapes[k][1] == p.rp) return k;
+    return 1;
+}
+
+// Tiles of simulation s with ns bodies in blocks of B: nb_s (nb_s + 1) / 2,
+// nb_s = ceil(ns / B).
+long long pairs_tiles(long long ns, int B) {
+    const long long nb = (ns + B - 1) / B;
     return nb * (nb + 1) / 2;
 }
 
 int launch_gravity_pairs_batched(const float4 *pos, int n, int n_gas, const int4 *d_sims,
                                  const long long *d_tile_off, int n_sims, long long n_tiles,
-                                 void *d_scales, float G, float eps, float4 *out, int flags,
-                                 void *d_work, cudaStream_t st) {
-    return pairs_launch(pos, n, n_gas, G, eps, out, flags, d_work, 0, 0,
-                        PairsPlan{GP_THREADS, GP_RP, -1}, d_sims, d_tile_off, n_sims, n_tiles,
-                        static_cast<PairsScale *>(d_scales), st);
+                                 int shape, void *d_scales, float G, float eps, float4 *out,
+                                 int flags, void *d_work, cudaStream_t st) {
+    if (shape < 0 || shape >= kPairsNumShapes) return SPH_ERR_INVALID_ARG;
+    const PairsPlan plan{kPairsShapes[shape][0], kPairsShapes[shape][1], -1};
+    return pairs_launch(pos, n, n_gas, G, eps, out, flags, d_work, 0, 0, plan, d_sims, d_tile_off,
+                        n_sims, n_tiles, static_cast<PairsScale *>(d_scales), st);
 }
 
 }  // namespace sphgb

@@ -59,12 +59,17 @@ int launch_gravity_batched(const float4 *pos, const int4 *sims, const int2 *unit
 int gravity_num_sms();
 // gravity_pairs.cu: tiles of one simulation with ns bodies, and the pair-once
 // evaluation of a batch (sims (g0, ng, d0, nd), tile_off[n_sims + 1])
-long long pairs_tiles(long long ns);
+// in blocks of B bodies; the block shapes of the pair-once plans, their
+// block sizes and the shape the current plan names
+constexpr int kPairsNumShapes = 4;
+long long pairs_tiles(long long ns, int B);
+int pairs_shape_block(int shape);
+int pairs_current_shape();
 size_t pairs_scale_bytes();   // bytes of one simulation's fixed-point scale
 int launch_gravity_pairs_batched(const float4 *pos, int n, int n_gas, const int4 *d_sims,
                                  const long long *d_tile_off, int n_sims, long long n_tiles,
-                                 void *d_scales, float G, float eps, float4 *out, int flags,
-                                 void *d_work, cudaStream_t st);
+                                 int shape, void *d_scales, float G, float eps, float4 *out,
+                                 int flags, void *d_work, cudaStream_t st);
 // device address of the gravity kernels' status word (SPH_FLAG_*)
 int *gravity_flags_device();
 // true while sph_gravity_tune has fixed a one-sided launch plan

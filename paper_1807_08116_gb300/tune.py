@@ -172,3 +172,22 @@ def tune_grid(sim, shifts=(-1, 0, 1), reps=3, apply=True):
     # leave the context's sort and lists as the step expects them
     build()
     return best, res
+
+
+def tune_batch_pairs_plan(batch, pos_m, work, G=1.0, eps=0.01, shapes=None, reps=2, apply=True):
+    """Time pp_gravity_pairs_batched on a batch for every block shape; fix the
+    fastest plan if apply (else restore the default).  Returns ((threads, R),
+    {shape: ms})."""
+    out = torch.empty_like(pos_m)
+    res = {}
+    try:
+        for threads, R in shapes or PAIRS_SHAPES:
+            nv.pp_gravity_pairs_plan(threads, R, -1)
+            res[(threads, R)] = _time(lambda: nv.pp_gravity_pairs_batched(batch, pos_m, out, work, G, eps),
+                                      reps)
+    finally:
+        nv.pp_gravity_pairs_plan(0)
+    best = min(res, key=res.get)
+    if apply:
+        nv.pp_gravity_pairs_plan(best[0], best[1], -1)
+    return best, res

@@ -214,7 +214,9 @@ def _batch_ics():
             ics.single_halo(2, 1, seed=35)]
 
 
-def test_batched_matches_oracle_per_simulation(orc, low_threshold):
+@pytest.mark.parametrize("shape", [(128, 8), (128, 6), (128, 10), (256, 8)])
+def test_batched_matches_oracle_per_simulation(orc, low_threshold, shape):
+    # every block shape a plan may name: blocks of 1024, 768, 1280, 2048 bodies
     torch = need_gpu()
     nv = low_threshold
     from paper_1807_08116_gb300.sim import assemble_batch
@@ -222,14 +224,18 @@ def test_batched_matches_oracle_per_simulation(orc, low_threshold):
     ic, go, do, so = assemble_batch(lst)
     batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
     pm = torch.as_tensor(pos_m_of(ic["r"], ic["m"]), device="cuda")
-    out = torch.full_like(pm, float("nan"))
     work = nv.pp_gravity_pairs_workspace(pm.shape[0])
-    nv.pp_gravity_pairs_batched(batch, pm, out, work, flags=nv.SPH_GRAV_POTENTIAL)
-    torch.cuda.synchronize()
-    got = out.cpu().numpy().astype(np.float64)
-    again = torch.full_like(pm, float("nan"))
-    nv.pp_gravity_pairs_batched(batch, pm, again, work, flags=nv.SPH_GRAV_POTENTIAL)
-    assert np.array_equal(again.cpu().numpy().astype(np.float64), got)   # reproducible
+    nv.pp_gravity_pairs_plan(*shape)
+    try:
+        out = torch.full_like(pm, float("nan"))
+        nv.pp_gravity_pairs_batched(batch, pm, out, work, flags=nv.SPH_GRAV_POTENTIAL)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+        again = torch.full_like(pm, float("nan"))
+        nv.pp_gravity_pairs_batched(batch, pm, again, work, flags=nv.SPH_GRAV_POTENTIAL)
+        assert np.array_equal(again.cpu().numpy().astype(np.float64), got)   # reproducible
+    finally:
+        nv.pp_gravity_pairs_plan(0)
     for s, d in enumerate(lst):
         cols = np.concatenate([np.arange(go[s], go[s + 1]), ic["n_gas"] + np.arange(do[s], do[s + 1])])
         acc, pot = orc.gravity(pos_m_of(d["r"], d["m"]))
