@@ -575,7 +575,9 @@ def run_ensemble(args):
     if flags:
         raise RuntimeError(f"device flags {flags} in the batched run")
 
-    # (b) one simulation at a time
+    # (b) one simulation at a time, each launch with the library's default
+    # pair-once plan (the tuned plan was chosen for the batched launch)
+    nv.pp_gravity_pairs_plan(0)
     sims = [Simulation(d) for d in lst]
     for sm in sims:
         sm.initial_rhs()
