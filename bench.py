@@ -598,6 +598,8 @@ def run_ensemble(args):
         worst = max(worst, float(np.abs(rb[bsim.sim_slices(k)] - r).max() / max(np.abs(r).max(), 1e-30)))
     # stage breakdown of one more batched step (eager, outside the timed region,
     # after the comparison of positions)
+    if best_plan:
+        nv.pp_gravity_pairs_plan(best_plan[0], best_plan[1], -1)
     ev = nv.StageEvents()
     bsim.state.events = ev.ptr
     bsim.step(dt, check=False)
