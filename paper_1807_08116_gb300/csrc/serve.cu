@@ -182,7 +182,6 @@ struct sph_server {
     std::vector<uint64_t> resident;
     uint64_t next_id = 1;
     std::mutex mu;
-    double min_job_bytes_factor = 1.0;
 };
 
 namespace {

@@ -529,7 +529,6 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
     __shared__ int s_cnt[kMaxLevels];
     __shared__ unsigned s_hmax[kMaxLevels];
     __shared__ int s_seg[SEG_CHUNK];
-    __shared__ long long s_pre;
     const int tid = threadIdx.x;
     const long long gtid = (long long)blockIdx.x * FS_THREADS + tid;
     const long long gstride = (long long)gridDim.x * FS_THREADS;
@@ -690,7 +689,6 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
         atomicAdd(&a.lvl_count[tid], s_cnt[tid]);
         atomicMax(&a.lvl_hmax[tid], s_hmax[tid]);
     }
-    (void)s_pre;
 }
 
 int launch_sort_fused(const SortArgs &a, cudaStream_t st) {
