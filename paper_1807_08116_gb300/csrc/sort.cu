@@ -504,8 +504,9 @@ struct RevSeg {   // reverse part of neighbour row s, clipped to the list capaci
 //      scans its chunk from the total of the chunks before it
 //   D  scatter with the atomic cursor (SP4), which drives the counts back
 //      to zero
-//   E  rank inside the buckets; F  block sort of buckets over 64 members
-//   G  sorted copies and the statistics over the sorted order
+//   E  rank inside the buckets, in the order of the scatter's slots, with
+//      each particle's sorted copy and statistics written at its final slot
+//   F  block sort of the buckets over 64 members, then theirs
 // The extremes are reduced as atomicMax of ~ordered(min) and ordered(max),
 // so 0 is the neutral value: the workspace starts zeroed, and block 0 puts
 // them back to 0 once every block has read them (phase C).
@@ -520,6 +521,44 @@ __device__ __forceinline__ void block_max_to(unsigned v, unsigned *shared5, int 
     if ((threadIdx.x & 31) == 0) atomicMax(&shared5[slot], v);
     __syncthreads();
     if (threadIdx.x == 0 && shared5[slot]) atomicMax(global, shared5[slot]);
+}
+
+// Particle i placed at sorted slot f (i < 0: this lane has none): its sorted
+// copies, and the bucket / super-cell / level statistics, aggregated over the
+// lanes that share a value (one atomic per run).  Called by all 32 lanes of a
+// warp together.
+__device__ __forceinline__ void place_sorted(const SortArgs &a, const GridDev &g, int i, int f,
+                                             int *s_cnt, unsigned *s_hmax) {
+    const int lane = threadIdx.x & 31;
+    int l = -1, k = -1;
+    unsigned hb = 0u, sbit = 0xffffffffu;   // no super-cell bit reaches 2^31
+    if (i >= 0) {
+        const float4 p = a.pos_h[i];
+        a.pos_h_s[f] = p;
+        const int sim = a.sim_of ? a.sim_of[i] : 0;
+        if (a.sim_s) a.sim_s[f] = sim;
+        int cx, cy, cz;
+        k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
+        hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;
+        if (a.occ)
+            sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
+                             l + kMaxLevels * sim, a.log2_B);
+    }
+    {
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        const unsigned m = __reduce_max_sync(peers, hb);
+        if (k >= 0 && lane == __ffs(peers) - 1 && m > 0u) atomicMax(&a.hmax_cell[k], m);
+    }
+    if (a.occ) {
+        const unsigned peers = __match_any_sync(0xffffffffu, sbit);
+        if (k >= 0 && lane == __ffs(peers) - 1) atomicOr(&a.occ[sbit >> 5], 1u << (sbit & 31));
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    const unsigned hpeer = __reduce_max_sync(peers, hb);
+    if (l >= 0 && lane == __ffs(peers) - 1) {
+        atomicAdd(&s_cnt[l], __popc(peers));
+        atomicMax(&s_hmax[l], hpeer);
+    }
 }
 
 __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
@@ -624,64 +663,51 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
     }
     grid.sync();
 
-    // E: rank inside the buckets (ascending original index)
-    for (long long i = gtid; i < n; i += gstride) {
-        const int k = a.key[i];
-        const int s = a.start[k], e = a.start[k + 1];
-        if (e - s > RANK_MAX) {
-            if (a.tmp[s] == (int)i) a.long_list[atomicAdd(a.long_count, 1)] = k;
-            continue;
+    // E: rank inside the buckets (ascending original index), taken in the
+    // order of the scatter's slots: the thread of slot j ranks the particle
+    // that landed there among its bucket's members (adjacent slots, so the
+    // bucket reads are shared by a warp) and puts it, its sorted copy and its
+    // statistics in its final slot; only the particle's own data is a random
+    // read.  Buckets of more than RANK_MAX members are queued for phase F.
+    // The trip count is warp-uniform so that the warp-wide matches see
+    // every lane.
+    const int lane = tid & 31;
+    for (long long w0 = gtid - lane; w0 < n; w0 += gstride) {
+        const long long j = w0 + lane;
+        int i = -1, k = -1, s = 0, e = 0;
+        if (j < n) {
+            i = a.tmp[j];
+            k = a.key[i];
+            s = a.start[k];
+            e = a.start[k + 1];
+            if (e - s > RANK_MAX) {
+                if (j == s) a.long_list[atomicAdd(a.long_count, 1)] = k;
+                i = -1;   // placed and counted in phase F
+            }
         }
-        int r = 0;
-        for (int q = s; q < e; ++q) r += a.tmp[q] < (int)i;
-        a.perm[s + r] = (int)i;
+        int f = -1;
+        if (i >= 0) {
+            int r = 0;
+            for (int q = s; q < e; ++q) r += a.tmp[q] < i;
+            f = s + r;
+            a.perm[f] = i;
+        }
+        place_sorted(a, g, i, f, s_cnt, s_hmax);
     }
     grid.sync();
 
-    // F: the long buckets, one block each
+    // F: the long buckets, one block each, then their sorted copies and
+    // statistics
     {
         const int nl = *a.long_count;
         for (int w = blockIdx.x; w < nl; w += gridDim.x) {
             const int k = a.long_list[w];
-            segsort_one(a.start[k], a.start[k + 1], a.tmp, a.perm, a.perm, s_seg);
-        }
-    }
-    grid.sync();
-
-    // G: sorted copies and the statistics (warp-uniform trip count, so the
-    // warp-wide matches see every lane)
-    const int lane = tid & 31;
-    for (long long w0 = gtid - lane; w0 < n; w0 += gstride) {
-        const long long j = w0 + lane;
-        int l = -1, k = -1;
-        unsigned hb = 0u, sbit = 0xffffffffu;
-        if (j < n) {
-            const int i = a.perm[j];
-            const float4 p = a.pos_h[i];
-            a.pos_h_s[j] = p;
-            const int sim = a.sim_of ? a.sim_of[i] : 0;
-            if (a.sim_s) a.sim_s[j] = sim;
-            int cx, cy, cz;
-            k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
-            hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;
-            if (a.occ)
-                sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
-                                 l + kMaxLevels * sim, a.log2_B);
-        }
-        {
-            const unsigned peers = __match_any_sync(0xffffffffu, k);
-            const unsigned m = __reduce_max_sync(peers, hb);
-            if (k >= 0 && lane == __ffs(peers) - 1 && m > 0u) atomicMax(&a.hmax_cell[k], m);
-        }
-        if (a.occ) {
-            const unsigned peers = __match_any_sync(0xffffffffu, sbit);
-            if (k >= 0 && lane == __ffs(peers) - 1) atomicOr(&a.occ[sbit >> 5], 1u << (sbit & 31));
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, l);
-        const unsigned hpeer = __reduce_max_sync(peers, hb);
-        if (l >= 0 && lane == __ffs(peers) - 1) {
-            atomicAdd(&s_cnt[l], __popc(peers));
-            atomicMax(&s_hmax[l], hpeer);
+            const int s = a.start[k], e = a.start[k + 1];
+            segsort_one(s, e, a.tmp, a.perm, a.perm, s_seg);
+            for (int f0 = s; f0 < e; f0 += FS_THREADS) {
+                const int f = f0 + tid;
+                place_sorted(a, g, f < e ? a.perm[f] : -1, f, s_cnt, s_hmax);
+            }
         }
     }
     __syncthreads();
