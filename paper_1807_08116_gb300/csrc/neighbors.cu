@@ -52,16 +52,17 @@ __device__ __forceinline__ void search_box(float x, float R, float x0, float inv
     hi = cell_of(__fadd_rn(x, m), x0, inv_c);
 }
 
-// Distance, in cell units, from a row at u = (x - x0) / csz to cell c,
-// less the rounding margin m (cell units); uh = u - 1/2.
-// The end cells also hold everything clamped into them, so they are open on
-// their outer side (EDGE: the box may touch them).  The margin m covers the
-// rounding of u, of this expression and of the neighbour predicate: the cut
-// never drops a cell that holds a row's neighbour (see search_box).
+// Distance, in cell units, from a row at u = (x - x0) / csz to cell c (the
+// cell coordinate as a float, exact below 2^24), less the rounding margin m
+// (cell units); uh = u - 1/2.  The end cells also hold everything clamped
+// into them, so they are open on their outer side (EDGE: the box may touch
+// them).  The margin m covers the rounding of u, of this expression and of
+// the neighbour predicate: the cut never drops a cell that holds a row's
+// neighbour (see search_box).
 template <bool EDGE>
-__device__ __forceinline__ float cell_gap_u(float uh, int c, float m_half) {
-    float d = fmaxf(fabsf(uh - (float)c) - m_half, 0.0f);   // m_half = 1/2 + m
-    if (EDGE && ((c == 0 && uh < 0.0f) || (c == kCellMax && uh > (float)kCellMax))) d = 0.0f;
+__device__ __forceinline__ float cell_gap(float uh, float c, float m_half) {
+    float d = fmaxf(fabsf(uh - c) - m_half, 0.0f);   // m_half = 1/2 + m
+    if (EDGE && ((c == 0.0f && uh < 0.0f) || (c == (float)kCellMax && uh > (float)kCellMax))) d = 0.0f;
     return d;
 }
 
@@ -256,30 +257,69 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                     }
                     const unsigned live = __ballot_sync(kFull, s < e);
                     if (live == 0u) continue;
+                    const float ftx = (float)tx, fty = (float)tyy, ftz = (float)tz;
                     // the bucket's max h in cell units, by the lane that read it
                     const float hmc = __fmul_rn(__uint_as_float(hm), inv_c);
                     // keep the cells some row of the group can reach: within
                     // h_i + hmax of the bucket, widened by the rounding margins
-                    // (a conservative cut, as the box is)
+                    // (a conservative cut, as the box is).  The pairs (member,
+                    // live cell) are taken by the shorter loop: over the live
+                    // cells with a member per lane, or over the members with a
+                    // cell per lane; both evaluate the same expression.
                     unsigned want = 0u;
-                    for (unsigned lv = live; lv; lv &= lv - 1u) {
-                        const int t = __ffs(lv) - 1;
-                        const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
-                                  cz = __shfl_sync(kFull, tz, t);
-                        const float reach = ihw + __shfl_sync(kFull, hmc, t);
-                        float dx, dy, dz;
-                        if (edge) {
-                            dx = cell_gap_u<true>(uhx, cx, mhx);
-                            dy = cell_gap_u<true>(uhy, cy, mhy);
-                            dz = cell_gap_u<true>(uhz, cz, mhz);
-                        } else {
-                            dx = cell_gap_u<false>(uhx, cx, mhx);
-                            dy = cell_gap_u<false>(uhy, cy, mhy);
-                            dz = cell_gap_u<false>(uhz, cz, mhz);
+                    if (__popc(part) < __popc(live)) {
+                        bool mine = false;
+                        for (unsigned mv = part; mv; mv &= mv - 1u) {
+                            const int m = __ffs(mv) - 1;
+                            const float muhx = __shfl_sync(kFull, uhx, m), muhy = __shfl_sync(kFull, uhy, m),
+                                        muhz = __shfl_sync(kFull, uhz, m);
+                            const float mmhx = __shfl_sync(kFull, mhx, m), mmhy = __shfl_sync(kFull, mhy, m),
+                                        mmhz = __shfl_sync(kFull, mhz, m);
+                            const float reach = __shfl_sync(kFull, ihw, m) + hmc;
+                            float dx, dy, dz;
+                            if (edge) {
+                                dx = cell_gap<true>(muhx, ftx, mmhx);
+                                dy = cell_gap<true>(muhy, fty, mmhy);
+                                dz = cell_gap<true>(muhz, ftz, mmhz);
+                            } else {
+                                dx = cell_gap<false>(muhx, ftx, mmhx);
+                                dy = cell_gap<false>(muhy, fty, mmhy);
+                                dz = cell_gap<false>(muhz, ftz, mmhz);
+                            }
+                            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            mine |= !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
                         }
-                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const bool need = in && !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
-                        if (__ballot_sync(kFull, need)) want |= 1u << t;
+                        want = __ballot_sync(kFull, mine) & live;
+                    } else {
+                        // cells of the batch that start a new (y, z) row: the y
+                        // and z part of the distance is taken once per row
+                        const int up_y = __shfl_up_sync(kFull, tyy, 1), up_z = __shfl_up_sync(kFull, tz, 1);
+                        const unsigned rowst = __ballot_sync(kFull, lane == 0 || tyy != up_y || tz != up_z);
+                        float yz = 0.0f;
+                        unsigned seen = 0u;
+                        for (unsigned lv = live; lv; lv &= lv - 1u) {
+                            const int t = __ffs(lv) - 1;
+                            const float cx = __shfl_sync(kFull, ftx, t);
+                            const float reach = ihw + __shfl_sync(kFull, hmc, t);
+                            const unsigned upto = (2u << t) - 1u;
+                            if (rowst & upto & ~seen) {
+                                const float cy = __shfl_sync(kFull, fty, t), cz = __shfl_sync(kFull, ftz, t);
+                                float dy, dz;
+                                if (edge) {
+                                    dy = cell_gap<true>(uhy, cy, mhy);
+                                    dz = cell_gap<true>(uhz, cz, mhz);
+                                } else {
+                                    dy = cell_gap<false>(uhy, cy, mhy);
+                                    dz = cell_gap<false>(uhz, cz, mhz);
+                                }
+                                yz = fmaf(dy, dy, dz * dz);
+                            }
+                            seen = upto;
+                            const float dx = edge ? cell_gap<true>(uhx, cx, mhx) : cell_gap<false>(uhx, cx, mhx);
+                            const float d2 = fmaf(dx, dx, yz);
+                            const bool need = in && !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
+                            if (__ballot_sync(kFull, need)) want |= 1u << t;
+                        }
                     }
                     // the candidates of the kept cells, numbered in cell order
                     const int len = ((want >> lane) & 1u) ? e - s : 0;
@@ -318,10 +358,11 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         const int nok = __popc(okm);
                         __syncwarp();   // the previous batch has been read
                         if (ok) {
+                            // coordinates negated: p + (-q) rounds as p - q
                             const int slot = __popc(okm & ((1u << lane) - 1u));
-                            sqx[slot] = q.x;
-                            sqy[slot] = q.y;
-                            sqz[slot] = q.z;
+                            sqx[slot] = -q.x;
+                            sqy[slot] = -q.y;
+                            sqz[slot] = -q.z;
                             sqh[slot] = q.w;
                             sj[slot] = jl;
                         }
@@ -345,9 +386,9 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                             const float2 qy2 = *reinterpret_cast<const float2 *>(sqy + u);
                             const float2 qz2 = *reinterpret_cast<const float2 *>(sqz + u);
                             const float2 qh2 = *reinterpret_cast<const float2 *>(sqh + u);
-                            const float2 dx = __fadd2_rn(px2, make_float2(-qx2.x, -qx2.y));
-                            const float2 dy = __fadd2_rn(py2, make_float2(-qy2.x, -qy2.y));
-                            const float2 dz = __fadd2_rn(pz2, make_float2(-qz2.x, -qz2.y));
+                            const float2 dx = __fadd2_rn(px2, qx2);
+                            const float2 dy = __fadd2_rn(py2, qy2);
+                            const float2 dz = __fadd2_rn(pz2, qz2);
                             const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)),
                                                          __fmul2_rn(dz, dz));
                             const float2 sh = __fadd2_rn(ph2, qh2);
