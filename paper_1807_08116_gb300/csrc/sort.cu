@@ -332,7 +332,9 @@ __global__ void bucket_rank_kernel(const int *__restrict__ key, int n, const int
 
 constexpr int WARP_RANK_MAX = 64;
 
-// One warp per segment [begin(s), end(s)) of distinct values: each value's
+// One warp per 32 consecutive segments [begin(s), end(s)) of distinct
+// values: each lane reads the bounds of one segment, and the warp then ranks
+// the segments of 2 to WARP_RANK_MAX values one after another: each value's
 // place is the number of smaller values in the segment (counted over the
 // values held in registers, up to two per lane), written back in place.
 // Longer segments are queued for the block-per-segment pass.
@@ -342,31 +344,37 @@ __global__ void __launch_bounds__(256) seg_rank_kernel(Seg seg, int nseg, int *d
                                                        int *__restrict__ long_count) {
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= nseg) return;   // the whole warp
-    const int s = (int)w;
-    const int b = seg.begin(s), len = seg.end(s) - b;
-    if (len <= 1) return;
-    if (len > WARP_RANK_MAX) {
-        if (lane == 0) long_list[atomicAdd(long_count, 1)] = s;
-        return;
+    if (w * 32 >= nseg) return;   // the whole warp
+    const long long sl = w * 32 + lane;
+    int bl = 0, ll = 0;
+    if (sl < nseg) {
+        bl = seg.begin((int)sl);
+        ll = seg.end((int)sl) - bl;
+        if (ll > WARP_RANK_MAX) long_list[atomicAdd(long_count, 1)] = (int)sl;
     }
-    const int v0 = lane < len ? data[b + lane] : INT_MAX;
-    const int v1 = lane + 32 < len ? data[b + 32 + lane] : INT_MAX;
-    int r0 = 0, r1 = 0;
-    const int n0 = len < 32 ? len : 32;
-    for (int t = 0; t < n0; ++t) {
-        const int x = __shfl_sync(0xffffffffu, v0, t);
-        r0 += x < v0;
-        r1 += x < v1;
+    for (unsigned todo = __ballot_sync(0xffffffffu, ll >= 2 && ll <= WARP_RANK_MAX); todo;
+         todo &= todo - 1u) {
+        const int src = __ffs(todo) - 1;
+        const int b = __shfl_sync(0xffffffffu, bl, src), len = __shfl_sync(0xffffffffu, ll, src);
+        const int v0 = lane < len ? data[b + lane] : INT_MAX;
+        const int v1 = lane + 32 < len ? data[b + 32 + lane] : INT_MAX;
+        int r0 = 0, r1 = 0;
+        const int n0 = len < 32 ? len : 32;
+        for (int t = 0; t < n0; ++t) {
+            const int x = __shfl_sync(0xffffffffu, v0, t);
+            r0 += x < v0;
+            r1 += x < v1;
+        }
+        for (int t = 32; t < len; ++t) {
+            const int x = __shfl_sync(0xffffffffu, v1, t - 32);
+            r0 += x < v0;
+            r1 += x < v1;
+        }
+        __syncwarp();
+        if (lane < len) data[b + r0] = v0;
+        if (lane + 32 < len) data[b + r1] = v1;
+        __syncwarp();
     }
-    for (int t = 32; t < len; ++t) {
-        const int x = __shfl_sync(0xffffffffu, v1, t - 32);
-        r0 += x < v0;
-        r1 += x < v1;
-    }
-    __syncwarp();
-    if (lane < len) data[b + r0] = v0;
-    if (lane + 32 < len) data[b + r1] = v1;
 }
 
 // One block per long segment.  Segments of up to SEG_CHUNK values are
@@ -776,8 +784,7 @@ int launch_segsort_rows(const int *nb_start, const int *own, int n, int cap, int
     SPH_CUDA_TRY(cudaMemsetAsync(long_count, 0, sizeof(int), st));
     RevSeg seg{nb_start, own, cap};
     if (n == 0) return SPH_OK;
-    seg_rank_kernel<<<blocks_for((long long)n * 32, 256), 256, 0, st>>>(seg, n, data, long_list,
-                                                                        long_count);
+    seg_rank_kernel<<<blocks_for(n, 256), 256, 0, st>>>(seg, n, data, long_list, long_count);
     segsort_long_kernel<<<1024, 256, 0, st>>>(seg, data, tmp, data, long_list, long_count);
     note_launch(2);
     SPH_LAUNCH_CHECK();
