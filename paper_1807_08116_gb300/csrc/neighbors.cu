@@ -26,7 +26,9 @@
 // that level.  A group walks the union of its members' search boxes with
 // warp-uniform loops, 32 cells at a time: lane t reads the bucket of cell
 // c0 + t, so one round trip covers 32 probes, and a cell is kept when it
-// passes the cell-distance cut of some member.  The candidates of the kept
+// lies within reach of the group's box (the members' extent, largest h and
+// largest rounding margins: one test per probed cell, by the lane that
+// probed it).  The candidates of the kept
 // cells are numbered in cell order and loaded 32 at a time (one per lane),
 // their level, cell and simulation are checked once by the lane that loaded
 // them, and the survivors are broadcast from shared memory to every member,
@@ -52,21 +54,24 @@ __device__ __forceinline__ void search_box(float x, float R, float x0, float inv
     hi = cell_of(__fadd_rn(x, m), x0, inv_c);
 }
 
-// Distance, in cell units, from a row at u = (x - x0) / csz to cell c (the
-// cell coordinate as a float, exact below 2^24), less the rounding margin m
-// (cell units); uh = u - 1/2.  The end cells also hold everything clamped
-// into them, so they are open on their outer side (EDGE: the box may touch
-// them).  The margin m covers the rounding of u, of this expression and of
-// the neighbour predicate: the cut never drops a cell that holds a row's
-// neighbour (see search_box).
-template <bool EDGE>
-__device__ __forceinline__ float cell_gap(float uh, float c, float m_half) {
-    float d = fmaxf(fabsf(uh - c) - m_half, 0.0f);   // m_half = 1/2 + m
-    if (EDGE && ((c == 0.0f && uh < 0.0f) || (c == (float)kCellMax && uh > (float)kCellMax))) d = 0.0f;
-    return d;
+constexpr unsigned kFull = 0xffffffffu;
+
+// FP32 <-> int maps that keep the order of non-NaN values, so that the
+// warp's integer min / max reductions give float extremes
+__device__ __forceinline__ int ord_of(float f) {
+    const int i = __float_as_int(f);
+    return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float float_of_ord(int i) {
+    return __int_as_float(i ^ ((i >> 31) & 0x7fffffff));
+}
+__device__ __forceinline__ float warp_minf(float f) {
+    return float_of_ord(__reduce_min_sync(kFull, ord_of(f)));
+}
+__device__ __forceinline__ float warp_maxf(float f) {
+    return float_of_ord(__reduce_max_sync(kFull, ord_of(f)));
 }
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNbWarps = 4;   // warps (row groups of 32) per block
 // rows whose cell lies within this many cells of the leader's join its group
 // (2, 3 and 4 measured; 3 and 4 within 1% of each other, 2 is 10% slower)
@@ -239,6 +244,14 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                 const float2 ph2 = in ? make_float2(p.w, p.w) : make_float2(__uint_as_float(0x7fc00000u),
                                                                            __uint_as_float(0x7fc00000u));
                 const float ihw = in ? __fmul_rn(p.w, inv_c) : 0.0f;
+                // the group's extent in cell units (extremes of its members'
+                // u - 1/2), its largest rounding margins and its largest h
+                const float inf = __int_as_float(0x7f800000);
+                const float AX = warp_minf(in ? uhx : inf), BX = warp_maxf(in ? uhx : -inf);
+                const float AY = warp_minf(in ? uhy : inf), BY = warp_maxf(in ? uhy : -inf);
+                const float AZ = warp_minf(in ? uhz : inf), BZ = warp_maxf(in ? uhz : -inf);
+                const float MX = warp_maxf(in ? mhx : 0.0f), MY = warp_maxf(in ? mhy : 0.0f),
+                            MZ = warp_maxf(in ? mhz : 0.0f), IH = warp_maxf(ihw);
                 const int NX = HX - LX + 1, NY = HY - LY + 1;
                 const int ncell = NX * NY * (HZ - LZ + 1);
                 for (int c0 = 0; c0 < ncell; c0 += 32) {
@@ -260,67 +273,27 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                     const float ftx = (float)tx, fty = (float)tyy, ftz = (float)tz;
                     // the bucket's max h in cell units, by the lane that read it
                     const float hmc = __fmul_rn(__uint_as_float(hm), inv_c);
-                    // keep the cells some row of the group can reach: within
-                    // h_i + hmax of the bucket, widened by the rounding margins
-                    // (a conservative cut, as the box is).  The pairs (member,
-                    // live cell) are taken by the shorter loop: over the live
-                    // cells with a member per lane, or over the members with a
-                    // cell per lane; both evaluate the same expression.
-                    unsigned want = 0u;
-                    if (__popc(part) < __popc(live)) {
-                        bool mine = false;
-                        for (unsigned mv = part; mv; mv &= mv - 1u) {
-                            const int m = __ffs(mv) - 1;
-                            const float muhx = __shfl_sync(kFull, uhx, m), muhy = __shfl_sync(kFull, uhy, m),
-                                        muhz = __shfl_sync(kFull, uhz, m);
-                            const float mmhx = __shfl_sync(kFull, mhx, m), mmhy = __shfl_sync(kFull, mhy, m),
-                                        mmhz = __shfl_sync(kFull, mhz, m);
-                            const float reach = __shfl_sync(kFull, ihw, m) + hmc;
-                            float dx, dy, dz;
-                            if (edge) {
-                                dx = cell_gap<true>(muhx, ftx, mmhx);
-                                dy = cell_gap<true>(muhy, fty, mmhy);
-                                dz = cell_gap<true>(muhz, ftz, mmhz);
-                            } else {
-                                dx = cell_gap<false>(muhx, ftx, mmhx);
-                                dy = cell_gap<false>(muhy, fty, mmhy);
-                                dz = cell_gap<false>(muhz, ftz, mmhz);
-                            }
-                            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            mine |= !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
-                        }
-                        want = __ballot_sync(kFull, mine) & live;
-                    } else {
-                        // cells of the batch that start a new (y, z) row: the y
-                        // and z part of the distance is taken once per row
-                        const int up_y = __shfl_up_sync(kFull, tyy, 1), up_z = __shfl_up_sync(kFull, tz, 1);
-                        const unsigned rowst = __ballot_sync(kFull, lane == 0 || tyy != up_y || tz != up_z);
-                        float yz = 0.0f;
-                        unsigned seen = 0u;
-                        for (unsigned lv = live; lv; lv &= lv - 1u) {
-                            const int t = __ffs(lv) - 1;
-                            const float cx = __shfl_sync(kFull, ftx, t);
-                            const float reach = ihw + __shfl_sync(kFull, hmc, t);
-                            const unsigned upto = (2u << t) - 1u;
-                            if (rowst & upto & ~seen) {
-                                const float cy = __shfl_sync(kFull, fty, t), cz = __shfl_sync(kFull, ftz, t);
-                                float dy, dz;
-                                if (edge) {
-                                    dy = cell_gap<true>(uhy, cy, mhy);
-                                    dz = cell_gap<true>(uhz, cz, mhz);
-                                } else {
-                                    dy = cell_gap<false>(uhy, cy, mhy);
-                                    dz = cell_gap<false>(uhz, cz, mhz);
-                                }
-                                yz = fmaf(dy, dy, dz * dz);
-                            }
-                            seen = upto;
-                            const float dx = edge ? cell_gap<true>(uhx, cx, mhx) : cell_gap<false>(uhx, cx, mhx);
-                            const float d2 = fmaf(dx, dx, yz);
-                            const bool need = in && !(d2 > reach * reach * (1.0f + 3.0517578125e-05f));
-                            if (__ballot_sync(kFull, need)) want |= 1u << t;
-                        }
+                    // keep the cells within reach of the group's box: the
+                    // distance from the box to the cell against the largest
+                    // h of the group plus the bucket's max h, widened by the
+                    // largest rounding margins.  Each of these bounds the
+                    // member's own value from the right side and rounding is
+                    // monotone, so every cell within a member's own reach
+                    // (and hence every cell its predicate can accept from) is
+                    // kept; the predicate alone decides the lists.
+                    float gx = fmaxf(fmaxf(AX - ftx, ftx - BX) - MX, 0.0f);
+                    float gy = fmaxf(fmaxf(AY - fty, fty - BY) - MY, 0.0f);
+                    float gz = fmaxf(fmaxf(AZ - ftz, ftz - BZ) - MZ, 0.0f);
+                    if (edge) {
+                        // the end cells also hold everything clamped into them
+                        if ((tx == 0 && AX < 0.0f) || (tx == kCellMax && BX > (float)kCellMax)) gx = 0.0f;
+                        if ((tyy == 0 && AY < 0.0f) || (tyy == kCellMax && BY > (float)kCellMax)) gy = 0.0f;
+                        if ((tz == 0 && AZ < 0.0f) || (tz == kCellMax && BZ > (float)kCellMax)) gz = 0.0f;
                     }
+                    const float gd2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                    const float greach = IH + hmc;
+                    const bool keep = !(gd2 > greach * greach * (1.0f + 3.0517578125e-05f));
+                    const unsigned want = __ballot_sync(kFull, s < e && keep);
                     // the candidates of the kept cells, numbered in cell order
                     const int len = ((want >> lane) & 1u) ? e - s : 0;
                     int incl = len;
@@ -434,6 +407,10 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
 // coarser partners with the top bit of the staged index.
 constexpr int kCopyThreads = 256;
 constexpr int kCopyLanes = 8;
+// entries a lane takes per round: their loads, the partners' row starts and
+// the cursor atomics of the reverse entries are issued together, so that
+// their round trips overlap instead of following one another
+constexpr int kCopyUnroll = 4;   // 1 and 8 measured slower
 __global__ void __launch_bounds__(kCopyThreads) nb_copy_kernel(NbArgs a) {
     const long long i = ((long long)blockIdx.x * kCopyThreads + threadIdx.x) / kCopyLanes;
     const int sl = threadIdx.x % kCopyLanes;
@@ -442,15 +419,34 @@ __global__ void __launch_bounds__(kCopyThreads) nb_copy_kernel(NbArgs a) {
     if (cnt > a.stage_k) return;
     const long long base = a.nb_start[i];
     const int *row = a.stage + i * a.stage_k;
-    for (int c = sl; c < cnt; c += kCopyLanes) {
-        const int v = row[c];
-        const int j = v & 0x7fffffff;
-        const long long w = base + c;
-        if (w < a.capacity) a.nb_idx[w] = j;
-        else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
-        if (v < 0) {
-            const int pos = atomicAdd(&a.rev[j], 1);
-            const long long wr = (long long)a.nb_start[j] + a.own[j] + pos;
+    for (int c0 = sl; c0 < cnt; c0 += kCopyLanes * kCopyUnroll) {
+        int v[kCopyUnroll];
+#pragma unroll
+        for (int u = 0; u < kCopyUnroll; ++u) {
+            const int c = c0 + u * kCopyLanes;
+            v[u] = c < cnt ? row[c] : 0;
+        }
+        long long at[kCopyUnroll];
+#pragma unroll
+        for (int u = 0; u < kCopyUnroll; ++u) {
+            const int c = c0 + u * kCopyLanes;
+            const int j = v[u] & 0x7fffffff;
+            if (c < cnt) {
+                const long long w = base + c;
+                if (w < a.capacity) a.nb_idx[w] = j;
+                else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
+            }
+            // a coarser partner: i goes to the reverse part of row j
+            at[u] = (c < cnt && v[u] < 0) ? (long long)a.nb_start[j] + a.own[j] : -1;
+        }
+        int pos[kCopyUnroll];
+#pragma unroll
+        for (int u = 0; u < kCopyUnroll; ++u)
+            pos[u] = at[u] >= 0 ? atomicAdd(&a.rev[v[u] & 0x7fffffff], 1) : 0;
+#pragma unroll
+        for (int u = 0; u < kCopyUnroll; ++u) {
+            if (at[u] < 0) continue;
+            const long long wr = at[u] + pos[u];
             if (wr < a.capacity) a.nb_idx[wr] = (int)i;
             else set_flag(a.flags, SPH_FLAG_NB_OVERFLOW);
         }
@@ -499,3 +495,4 @@ int launch_row_len(const int *own, const int *rev, int n, int *row_len, cudaStre
 }
 
 }  // namespace sphgb
+
