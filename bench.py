@@ -147,8 +147,18 @@ def stage_roofline(stage_ms, n, ng, nb_entries):
 # FP32-pipe operations per ordered interaction: the one-sided kernel does
 # 3 FADD + 3 FFMA + 3 FMUL + 3 FFMA (+1 MUFU); the pair-once kernel does 16
 # per unordered pair (3 FADD, 3 FFMA, 4 FMUL, 2 x 3 FFMA), i.e. 8 per
-# ordered interaction.
+# ordered interaction, and 14 (7 per ordered interaction) in tiles whose
+# bodies all have the same mass (the mass products leave the pair term).
 FP32_OPS = {"pp_gravity_kernel": 12, "pp_gravity_pairs_kernel": 8}
+FP32_OPS_EQUAL_MASS = {"pp_gravity_kernel": 12, "pp_gravity_pairs_kernel": 7}
+
+
+def fp32_ops(kernel, masses):
+    """FP32-pipe operations per ordered interaction of the kernel on these
+    masses (every tile takes the equal-mass form when all masses are equal)."""
+    m = np.asarray(masses)
+    equal = m.size > 0 and bool(np.all(m == m.flat[0]))
+    return (FP32_OPS_EQUAL_MASS if equal else FP32_OPS)[kernel]
 
 
 def make_ic(name, rank=0):
@@ -428,6 +438,7 @@ def run_ours(args):
         kernel = "pp_gravity_kernel"
         R, S = nv.sph_gravity_plan(n)
         plan = {"scheme": "one-sided", "targets_per_thread": R, "cluster_split": S}
+    ops = fp32_ops(kernel, sim.t["mass"].cpu().numpy())
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz_max = sm_max_mhz(clk)
     mhz_run = float(clk["sm_mhz"]) if clk and clk.get("sm_mhz") else mhz_max
@@ -438,8 +449,8 @@ def run_ours(args):
             "traffic": args.gfc_traffic if args.gfc_traffic is not None else gfc_traffic(n, kernel),
             "kernel": kernel, "interactions_per_s": ips,
             "flop_per_interaction": FLOP_PER_INTERACTION,
-            "fp32_ops_per_interaction": FP32_OPS[kernel],
-            "fp32_pipe_frac": FP32_OPS[kernel] * ips / fp32_lane_ops_per_s(sms, mhz_max),
+            "fp32_ops_per_interaction": ops,
+            "fp32_pipe_frac": ops * ips / fp32_lane_ops_per_s(sms, mhz_max),
             "sm_count": sms, "sm_max_mhz": mhz_max, "sm_mhz": mhz_run,
             "peak_at_sm_mhz": peak_run, "frac_at_sm_mhz": achieved / peak_run,
             "peak_note": f"FP32 pipe {sms} SM x {FP32_LANES_PER_SM} lanes x 2 flop x {mhz_max:.0f} MHz "
@@ -862,7 +873,8 @@ def run_gravity(args):
                       "n": n, "ms_per_launch": ms, "steps": args.steps, "warmup": args.warmup,
                       "kernel": kernel, "tflops_20flop": FLOP_PER_INTERACTION * ips / 1e12,
                       "frac_of_fp32_peak": FLOP_PER_INTERACTION * ips / 1e12 / fp32_peak_tflops(sms, mhz),
-                      "fp32_pipe_frac": FP32_OPS[kernel] * ips / fp32_lane_ops_per_s(sms, mhz),
+                      "fp32_pipe_frac": fp32_ops(kernel, x[:, 3].cpu().numpy()) * ips /
+                      fp32_lane_ops_per_s(sms, mhz),
                       "sm_count": sms, "sm_max_mhz": mhz, "plan": plan}), flush=True)
     return 0
 

@@ -6,7 +6,9 @@
 //     inv = (|r_j - r_i|^2 + eps^2)^(-1/2),  w = inv^3
 // serves both bodies: g_i += m_j w (r_j - r_i) and g_j -= m_i w (r_j - r_i).
 // Per pair that is 16 FP32-pipe operations instead of 2 x 12 for the two
-// one-sided interactions.
+// one-sided interactions.  When every body of a tile has the same mass m0
+// (equal-mass particles, as in the paper's models), the sums leave the mass
+// out and take m0 once per tile sum: 14 operations per pair.
 //
 // Layout of the work:
 //  * bodies are cut into blocks of B = 1024 (128 threads x 8 targets); the
@@ -218,7 +220,7 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, float s1, float 
 // One slab (GP_SLAB sources starting at s0) of a tile.  SYM: also collect
 // the sums of the sources (off-diagonal tiles) into wpart[GP_SLAB][NC].
 // ---------------------------------------------------------------------------
-template <bool SYM, bool POT, int THREADS, int RP>
+template <bool SYM, bool POT, int THREADS, int RP, bool EQ>
 __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const float4 *__restrict__ dB,
                                           int s0, int lane, const float2 (&nx)[RP],
                                           const float2 (&ny)[RP], const float2 (&nz)[RP],
@@ -255,17 +257,33 @@ __device__ __forceinline__ void ring_slab(const float4 *__restrict__ dA, const f
                     if (s == tid + (2 * p + 1) * THREADS) inv.y = 0.f;
                 }
                 const float2 w = __fmul2_rn(__fmul2_rn(inv, inv), inv);
-                const float2 si = __fmul2_rn(w, qm);
-                ax[p] = __ffma2_rn(si, dx, ax[p]);
-                ay[p] = __ffma2_rn(si, dy, ay[p]);
-                az[p] = __ffma2_rn(si, dz, az[p]);
-                if (POT) ap[p] = __ffma2_rn(qm, inv, ap[p]);
-                if (SYM) {
-                    const float2 sj = __fmul2_rn(w, mi[p]);
-                    tx = __ffma2_rn(sj, dx, tx);
-                    ty = __ffma2_rn(sj, dy, ty);
-                    tz = __ffma2_rn(sj, dz, tz);
-                    if (POT) tp = __ffma2_rn(mi[p], inv, tp);
+                if (EQ) {
+                    // every body of the tile has the same mass: the sums
+                    // leave it out and take it once, when the tile's sums
+                    // are converted (one product per pair fewer on each side)
+                    ax[p] = __ffma2_rn(w, dx, ax[p]);
+                    ay[p] = __ffma2_rn(w, dy, ay[p]);
+                    az[p] = __ffma2_rn(w, dz, az[p]);
+                    if (POT) ap[p] = __fadd2_rn(inv, ap[p]);
+                    if (SYM) {
+                        tx = __ffma2_rn(w, dx, tx);
+                        ty = __ffma2_rn(w, dy, ty);
+                        tz = __ffma2_rn(w, dz, tz);
+                        if (POT) tp = __fadd2_rn(inv, tp);
+                    }
+                } else {
+                    const float2 si = __fmul2_rn(w, qm);
+                    ax[p] = __ffma2_rn(si, dx, ax[p]);
+                    ay[p] = __ffma2_rn(si, dy, ay[p]);
+                    az[p] = __ffma2_rn(si, dz, az[p]);
+                    if (POT) ap[p] = __ffma2_rn(qm, inv, ap[p]);
+                    if (SYM) {
+                        const float2 sj = __fmul2_rn(w, mi[p]);
+                        tx = __ffma2_rn(sj, dx, tx);
+                        ty = __ffma2_rn(sj, dy, ty);
+                        tz = __ffma2_rn(sj, dz, tz);
+                        if (POT) tp = __ffma2_rn(mi[p], inv, tp);
+                    }
                 }
             }
             if (SYM) {
@@ -361,17 +379,30 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
     }
     const PairsScale sc = scales[sim];
     const float sa1 = sc.s_acc1, sa2 = sc.s_acc2, sp1 = sc.s_pot1, sp2 = sc.s_pot2;
-    __syncthreads();
+    // A tile whose bodies all have the same mass m0 (and no padding) takes
+    // the sums without the mass factors, and m0 once per sum at the end.
+    const float m0 = pos[global_of(I * B)].w;
+    bool same = cnt == B && (I + 1) * B <= ns;
+    for (int q = tid; q < B; q += THREADS) same = same && dB[q].z == m0;
+#pragma unroll
+    for (int p = 0; p < RP; ++p) same = same && mi[p].x == m0 && mi[p].y == m0;
+    const bool eq = __syncthreads_and(same) != 0;
     const float2 e2 = make_float2(eps2, eps2);
     float *wpart = part + warp * GP_SLAB * NC;
     if (I != J) {
         for (int s0 = 0; s0 < cnt; s0 += GP_SLAB) {   // sources past cnt are massless padding
-            ring_slab<true, POT, THREADS, RP>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+            if (eq)
+                ring_slab<true, POT, THREADS, RP, true>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap,
+                                                        wpart, tid);
+            else
+                ring_slab<true, POT, THREADS, RP, false>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap,
+                                                         wpart, tid);
             __syncthreads();
             for (int q = tid; q < GP_SLAB * NC; q += THREADS) {
                 float v = 0.f;
 #pragma unroll
                 for (int w = 0; w < Sh::kWarps; ++w) v = __fadd_rn(v, part[w * GP_SLAB * NC + q]);
+                if (eq) v = __fmul_rn(v, m0);
                 const int comp = q % NC;
                 int j;
                 if (BATCH) j = sidx[s0 + q / NC];
@@ -383,12 +414,25 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
             __syncthreads();   // warp sums consumed before the next slab
         }
     } else {
-        for (int s0 = 0; s0 < cnt; s0 += GP_SLAB)
-            ring_slab<false, POT, THREADS, RP>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap, wpart, tid);
+        for (int s0 = 0; s0 < cnt; s0 += GP_SLAB) {
+            if (eq)
+                ring_slab<false, POT, THREADS, RP, true>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap,
+                                                         wpart, tid);
+            else
+                ring_slab<false, POT, THREADS, RP, false>(dA, dB, s0, lane, nx, ny, nz, mi, e2, ax, ay, az, ap,
+                                                          wpart, tid);
+        }
     }
     // the tile's sums of its targets
 #pragma unroll
     for (int p = 0; p < RP; ++p) {
+        if (eq) {
+            const float2 m2 = make_float2(m0, m0);
+            ax[p] = __fmul2_rn(ax[p], m2);
+            ay[p] = __fmul2_rn(ay[p], m2);
+            az[p] = __fmul2_rn(az[p], m2);
+            if (POT) ap[p] = __fmul2_rn(ap[p], m2);
+        }
         int ia, ib;
         if (BATCH) {
             ia = tidx[tid + (2 * p) * THREADS];

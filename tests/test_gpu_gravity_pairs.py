@@ -78,6 +78,31 @@ def test_ragged_block_counts(orc, low_threshold, n):
     assert prms <= RMS_TOL and pmx <= MAX_TOL, (prms, pmx)
 
 
+@pytest.mark.parametrize("case", ["equal", "one_block_heavier", "ragged_equal", "one_body_off"])
+def test_equal_mass_tiles(orc, low_threshold, case):
+    # tiles whose bodies all share one mass take the sums without the mass
+    # factors; tiles with another mass, a body off by one ulp, or a ragged
+    # last block take the general form: both against the oracle, with the
+    # potential, and the two forms agree where they meet
+    nv = low_threshold
+    n = 5000 if case == "ragged_equal" else 5120
+    rng = np.random.default_rng(11)
+    m = np.full(n, 1.0 / n, np.float32)
+    if case == "one_block_heavier":
+        m[2048:3072] *= np.float32(3.0)
+    if case == "one_body_off":
+        m[777] = np.nextafter(m[777], np.float32(1.0))
+    pm = pos_m_of(rng.normal(size=(n, 3)), m)
+    g = _pairs(pm, G=0.7, eps=0.05, flags=nv.SPH_GRAV_POTENTIAL)
+    acc, pot = orc.gravity(pm, G=0.7, eps=0.05)
+    rms, mx = err(g[:, :3], acc)
+    assert rms <= RMS_TOL and mx <= MAX_TOL, (case, rms, mx)
+    prms, pmx = err(g[:, 3:], pot[:, None])
+    assert prms <= RMS_TOL and pmx <= MAX_TOL, (case, prms, pmx)
+    mm = pm[:, 3].astype(np.float64)
+    assert np.abs((mm[:, None] * g[:, :3]).sum(0)).max() < 1e-5 * (mm[:, None] * np.abs(g[:, :3])).sum()
+
+
 def test_single_halo_all_rows_and_momentum(orc, low_threshold):
     nv = low_threshold
     d = ics.single_halo(8192, 8192, seed=0)
