@@ -331,13 +331,16 @@ __global__ void bucket_rank_kernel(const int *__restrict__ key, int n, const int
 }
 
 constexpr int WARP_RANK_MAX = 64;
+constexpr int LANE_RANK_MAX = 8;
 
 // One warp per 32 consecutive segments [begin(s), end(s)) of distinct
-// values: each lane reads the bounds of one segment, and the warp then ranks
-// the segments of 2 to WARP_RANK_MAX values one after another: each value's
-// place is the number of smaller values in the segment (counted over the
-// values held in registers, up to two per lane), written back in place.
-// Longer segments are queued for the block-per-segment pass.
+// values; each lane reads the bounds of one segment.  Segments of 2 to
+// LANE_RANK_MAX values (nearly all of them) are sorted by their own lane in
+// registers: every value's place is the number of smaller values, and the
+// loads of the 32 segments are in flight together.  The warp then ranks the
+// segments of LANE_RANK_MAX + 1 to WARP_RANK_MAX values one after another
+// (counted over the values held in registers, up to two per lane), written
+// back in place.  Longer segments are queued for the block-per-segment pass.
 template <class Seg>
 __global__ void __launch_bounds__(256) seg_rank_kernel(Seg seg, int nseg, int *data,
                                                        int *__restrict__ long_list,
@@ -352,7 +355,19 @@ __global__ void __launch_bounds__(256) seg_rank_kernel(Seg seg, int nseg, int *d
         ll = seg.end((int)sl) - bl;
         if (ll > WARP_RANK_MAX) long_list[atomicAdd(long_count, 1)] = (int)sl;
     }
-    for (unsigned todo = __ballot_sync(0xffffffffu, ll >= 2 && ll <= WARP_RANK_MAX); todo;
+    if (ll >= 2 && ll <= LANE_RANK_MAX) {
+        int v[LANE_RANK_MAX];
+#pragma unroll
+        for (int u = 0; u < LANE_RANK_MAX; ++u) v[u] = u < ll ? data[bl + u] : INT_MAX;
+#pragma unroll
+        for (int u = 0; u < LANE_RANK_MAX; ++u) {
+            int r = 0;
+#pragma unroll
+            for (int t = 0; t < LANE_RANK_MAX; ++t) r += v[t] < v[u];
+            if (u < ll) data[bl + r] = v[u];
+        }
+    }
+    for (unsigned todo = __ballot_sync(0xffffffffu, ll > LANE_RANK_MAX && ll <= WARP_RANK_MAX); todo;
          todo &= todo - 1u) {
         const int src = __ffs(todo) - 1;
         const int b = __shfl_sync(0xffffffffu, bl, src), len = __shfl_sync(0xffffffffu, ll, src);

@@ -103,6 +103,37 @@ def test_forces_single_halo(orc, lanes):
     assert np.abs((m[:, None] * a[:, :3]).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(a[:, :3])).sum()
 
 
+def test_equal_mass_loops_match_the_general_ones(orc):
+    # with all gas masses equal, density and forces read m_j (and P_j) from
+    # the row's own particle and vel_s, and aux_s only for approaching pairs;
+    # one particle's mass one ulp off sends both passes through the general
+    # loops.  Rows that do not have that particle as a neighbour must come out
+    # bitwise the same either way, and both runs match the oracle.
+    d = ics.single_halo(8192, 8192, seed=0)
+    ph, mass, ve = _stirred(d)
+    assert np.all(mass == mass[0])
+    k = int(np.argmin(ph[:, 3]))   # the smallest h: the fewest rows reach it
+    off = mass.copy()
+    off[k] = np.nextafter(off[k], np.float32(1.0))
+    dist = np.linalg.norm(ph[:, :3].astype(np.float64) - ph[k, :3], axis=1)
+    clear = dist >= 1.01 * (ph[:, 3].astype(np.float64) + ph[k, 3])
+    assert clear.sum() > 8000
+    res = {}
+    rin = orc.density(ph, mass)[0].astype(np.float32)   # the same densities for both force passes
+    for name, m in (("equal", mass), ("mixed", off)):
+        _, rho, hn = _density(ph, m)
+        orho, _ = orc.density(ph, m)
+        r1, m1 = err(rho, orho)
+        assert r1 <= RHO_RMS and m1 <= RHO_MAX, (name, r1, m1)
+        a = _forces(ph, ve, m, rin)
+        oa, ode = orc.hydro(ph, ve, m, rin)
+        ra, ma = err(a[:, :3], oa)
+        assert ra <= RMS_TOL and ma <= MAX_TOL, (name, ra, ma)
+        res[name] = (rho, hn, a)
+    for x, y in zip(res["equal"], res["mixed"]):
+        assert np.array_equal(x[clear], y[clear])
+
+
 def test_forces_at_rest_and_without_viscosity(orc):
     d = ics.single_halo(4096, 0, seed=2)
     ph, mass, ve = _gas(d)      # gas at rest: pressure only
