@@ -222,14 +222,23 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                 if (a.occ && l > lg) {
                     // skip the level when none of the super-cells the box
                     // touches holds a particle of it (the rows' own level is
-                    // always occupied)
+                    // always occupied); one super-cell per lane, 32 per round
+                    // trip
+                    const int SX = LX >> kSuperShift, SY = LY >> kSuperShift, SZ = LZ >> kSuperShift;
+                    const int nsx = (HX >> kSuperShift) - SX + 1, nsy = (HY >> kSuperShift) - SY + 1;
+                    const int ns = nsx * nsy * ((HZ >> kSuperShift) - SZ + 1);
                     bool any = false;
-                    for (int sz = LZ >> kSuperShift; sz <= (HZ >> kSuperShift) && !any; ++sz)
-                        for (int sy = LY >> kSuperShift; sy <= (HY >> kSuperShift) && !any; ++sy)
-                            for (int sx = LX >> kSuperShift; sx <= (HX >> kSuperShift) && !any; ++sx) {
-                                const unsigned bit = super_bit(sx, sy, sz, l + kMaxLevels * sg, a.log2_B);
-                                any = (a.occ[bit >> 5] >> (bit & 31)) & 1u;
-                            }
+                    for (int b0 = 0; b0 < ns && !any; b0 += 32) {
+                        const int t = b0 + lane;
+                        bool hit = false;
+                        if (t < ns) {
+                            const int qx = t / nsx, qy = qx / nsy;
+                            const unsigned bit = super_bit(SX + (t - qx * nsx), SY + (qx - qy * nsy), SZ + qy,
+                                                           l + kMaxLevels * sg, a.log2_B);
+                            hit = (a.occ[bit >> 5] >> (bit & 31)) & 1u;
+                        }
+                        any = __any_sync(kFull, hit);
+                    }
                     if (!any) continue;
                 }
                 // the end cells are open on their outer side: only boxes that
