@@ -142,8 +142,8 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->grid = cv.take<GridDev>(1);
     c->red = cv.take<unsigned>(8);
     c->red_fused = cv.take<unsigned>(8);
-    // [0] status bits; [1], [2] set when the masses of the last density /
-    // force pass were not all equal (their equal-mass loops read fewer arrays)
+    // [0] status bits; [1] set when the masses of the last density pass were
+    // not all equal (its equal-mass loop reads no mass array)
     c->flags = cv.take<int>(4);
     // the scan's block totals, also the chunk totals of the one-launch sort,
     // whose grid they cap: room for a full resident grid (a few blocks per SM)
@@ -488,11 +488,11 @@ extern "C" int sph_forces(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, con
     HydroParams hp = hydro_params(ctx);
     int rc;
     if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
-                                n_gas, hp, ctx->vel_s, ctx->aux_s, ctx->flags + 2, st)))
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
         return rc;
     return launch_forces(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
                          ctx->nb_idx, (int)ctx->capacity, n_gas, hp, ctx->hydro_lanes,
-                         reinterpret_cast<float4 *>(d_acc_dedt), ctx->flags + 2, st);
+                         reinterpret_cast<float4 *>(d_acc_dedt), st);
 }
 
 extern "C" int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, const float *d_rho,
@@ -507,7 +507,7 @@ extern "C" int sph_cfl_dt(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e, con
     HydroParams hp = hydro_params(ctx);
     int rc;
     if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
-                                n_gas, hp, ctx->vel_s, ctx->aux_s, ctx->flags + 2, st)))
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
         return rc;
     return launch_cfl(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start, ctx->nb_idx,
                       (int)ctx->capacity, n_gas, hp, C_cfl,
@@ -530,11 +530,11 @@ extern "C" int sph_forces_cfl(sph_ctx *ctx, int32_t n_gas, const float *d_vel_e,
     HydroParams hp = hydro_params(ctx);
     int rc;
     if ((rc = launch_hydro_prep(reinterpret_cast<const float4 *>(d_vel_e), d_rho, d_mass, ctx->perm,
-                                n_gas, hp, ctx->vel_s, ctx->aux_s, ctx->flags + 2, st)))
+                                n_gas, hp, ctx->vel_s, ctx->aux_s, st)))
         return rc;
     return launch_forces(ctx->pos_h_s, ctx->vel_s, ctx->aux_s, ctx->perm, ctx->nb_start,
                          ctx->nb_idx, (int)ctx->capacity, n_gas, hp, ctx->hydro_lanes,
-                         reinterpret_cast<float4 *>(d_acc_dedt), ctx->flags + 2, st,
+                         reinterpret_cast<float4 *>(d_acc_dedt), st,
                          reinterpret_cast<const float4 *>(d_grav), C_cfl, d_dt_particle, d_dt_min,
                          dt_max);
 }

@@ -154,29 +154,22 @@ __global__ void gather_mass_kernel(const float *__restrict__ mass, const int *__
     flag_mixed_mass(differs, mixed);
 }
 
-// Sorted working copies for HFC: vel_s = (vx, vy, vz, P); aux_s = (m, rho,
+// Sorted working copies for HFC: vel_s = (vx, vy, vz, e); aux_s = (m, rho,
 // P = p / rho^2 = (gamma - 1) e / rho, c = sqrt(gamma (gamma - 1) e), 0 if e < 0).
-// P sits in both, so that a pass over equal masses needs aux_s only for
-// approaching pairs; *mixed flags masses that differ from mass[0].
 __global__ void hydro_prep_kernel(const float4 *__restrict__ vel_e, const float *__restrict__ rho,
                                   const float *__restrict__ mass, const int *__restrict__ perm,
                                   int n, HydroParams hp, float4 *__restrict__ vel_s,
-                                  float4 *__restrict__ aux_s, int *__restrict__ mixed) {
+                                  float4 *__restrict__ aux_s) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    bool differs = false;
-    if (j < n) {
-        const int o = perm[j];
-        const float4 v = vel_e[o];
-        const float r = rho[o];
-        const float m = mass[o];
-        const float gm1 = hp.gamma - 1.0f;
-        const float P = gm1 * v.w / r;
-        const float c = v.w >= 0.0f ? sqrtf(hp.gamma * gm1 * v.w) : 0.0f;
-        vel_s[j] = make_float4(v.x, v.y, v.z, P);
-        aux_s[j] = make_float4(m, r, P, c);
-        differs = !(m == mass[0]);
-    }
-    flag_mixed_mass(differs, mixed);
+    if (j >= n) return;
+    const int o = perm[j];
+    const float4 v = vel_e[o];
+    const float r = rho[o];
+    const float gm1 = hp.gamma - 1.0f;
+    const float P = gm1 * v.w / r;
+    const float c = v.w >= 0.0f ? sqrtf(hp.gamma * gm1 * v.w) : 0.0f;
+    vel_s[j] = v;
+    aux_s[j] = make_float4(mass[o], r, P, c);
 }
 
 // Hydrodynamic acceleration and heating of Eqs. 10-11, G lanes per row.
@@ -190,8 +183,7 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
               const float4 *__restrict__ aux_s, const int *__restrict__ perm,
               const int *__restrict__ nb_start, const int *__restrict__ nb_idx, int cap, int n,
               HydroParams hp, float4 *__restrict__ acc_out, const float4 *__restrict__ grav,
-              float C, float *__restrict__ dt_out, unsigned *__restrict__ dt_min_bits,
-              const int *__restrict__ mixed) {
+              float C, float *__restrict__ dt_out, unsigned *__restrict__ dt_min_bits) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / G, q = t % G;
     const bool valid = i < n;
@@ -212,60 +204,43 @@ forces_kernel(const float4 *__restrict__ pos_h_s, const float4 *__restrict__ vel
     Kahan ax, ay, az, de;
     ax.init(); ay.init(); az.init(); de.init();
     float s2_min = __int_as_float(0x7f800000), c_max = 0.0f, mu_max = 0.0f;
-    // All gas masses equal (*mixed == 0, without the CFL extrema, which need
-    // c_j of every pair): m_j = m_i and P_j from vel_s, so aux_s is read
-    // only for approaching pairs (rho_j and c_j of the viscosity).  The
-    // arithmetic is the same, so are the results.
-    auto row = [&](auto same) {
-        constexpr bool EQM = decltype(same)::value;
 #pragma unroll 4
-        for (int k = b + q; k < e; k += G) {
-            const int j = nb_idx[k];
-            if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
-            const float4 o = pos_h_s[j];
-            const float4 w = vel_s[j];
-            float4 aj = make_float4(ai.x, 0.0f, w.w, 0.0f);
-            if (!EQM) aj = aux_s[j];
-            const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
-            const float dvx = v.x - w.x, dvy = v.y - w.y, dvz = v.z - w.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-            const float r = r2 * rinv;
-            const float hij = 0.5f * (p.w + o.w);
-            const float ih = __fdividef(1.0f, hij);
-            // every product and sum of the pair term is rounded on its own
-            // (no contraction), so both loops give the same bits
-            const float tt = fmaxf(__fsub_rn(2.0f, __fmul_rn(r, ih)), 0.0f);
-            // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
-            const float f = kdw * (ih * ih * ih) * tt * tt * ih * rinv;
-            const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
-            float nu = 0.0f;
-            if (rv < 0.0f) {
-                if (EQM) {
-                    const float4 a2 = aux_s[j];
-                    aj.y = a2.y;
-                    aj.w = a2.w;
-                }
-                const float c_ij = 0.5f * (ai.w + aj.w);
-                const float mu = visc_mu(hij, rv, r2, hp.eta);
-                const float rho_ij = 0.5f * (ai.y + aj.y);
-                nu = __fdividef(__fmul_rn(mu, fmaf(hp.beta, mu, __fmul_rn(-hp.alpha, c_ij))), rho_ij);
-                if (CFL) mu_max = fmaxf(mu_max, -mu);
-            }
-            if (CFL) {
-                s2_min = fminf(s2_min, r2);
-                c_max = fmaxf(c_max, 0.5f * (ai.w + aj.w));
-            }
-            const float Pi = __fadd_rn(__fadd_rn(ai.z, aj.z), nu);
-            const float g = __fmul_rn(__fmul_rn(aj.x, Pi), f);   // m_j Pi_ij f
-            ax.add(__fmul_rn(-g, dx));
-            ay.add(__fmul_rn(-g, dy));
-            az.add(__fmul_rn(-g, dz));
-            de.add(__fmul_rn(__fmul_rn(0.5f, g), fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz))));
+    for (int k = b + q; k < e; k += G) {
+        const int j = nb_idx[k];
+        if ((unsigned)j >= (unsigned)n) continue;   // only after a flagged overflow
+        const float4 o = pos_h_s[j];
+        const float4 w = vel_s[j];
+        const float4 aj = aux_s[j];
+        const float dx = p.x - o.x, dy = p.y - o.y, dz = p.z - o.z;
+        const float dvx = v.x - w.x, dvy = v.y - w.y, dvz = v.z - w.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        const float r = r2 * rinv;
+        const float hij = 0.5f * (p.w + o.w);
+        const float ih = __fdividef(1.0f, hij);
+        const float tt = fmaxf(2.0f - r * ih, 0.0f);
+        // grad W_p = (dW_p/dxi) (dr / r) / h_ij = f * dr; zero at r = 0
+        const float f = kdw * (ih * ih * ih) * tt * tt * ih * rinv;
+        const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+        const float c_ij = 0.5f * (ai.w + aj.w);
+        float nu = 0.0f;
+        if (rv < 0.0f) {
+            const float mu = visc_mu(hij, rv, r2, hp.eta);
+            const float rho_ij = 0.5f * (ai.y + aj.y);
+            nu = __fdividef(mu * fmaf(hp.beta, mu, -hp.alpha * c_ij), rho_ij);
+            if (CFL) mu_max = fmaxf(mu_max, -mu);
         }
-    };
-    if (!CFL && *mixed == 0) row(std::true_type{});
-    else row(std::false_type{});
+        if (CFL) {
+            s2_min = fminf(s2_min, r2);
+            c_max = fmaxf(c_max, c_ij);
+        }
+        const float Pi = ai.z + aj.z + nu;
+        const float g = aj.x * Pi * f;   // m_j Pi_ij f
+        ax.add(-g * dx);
+        ay.add(-g * dy);
+        az.add(-g * dz);
+        de.add(0.5f * g * fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz)));
+    }
     const float sx = group_sum<G>(ax.s - ax.c, mask);
     const float sy = group_sum<G>(ay.s - ay.c, mask);
     const float sz = group_sum<G>(az.s - az.c, mask);
@@ -384,12 +359,10 @@ int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, co
 }
 
 int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
-                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, int *mixed,
-                      cudaStream_t st) {
+                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st) {
     if (n > 0) {
-        SPH_CUDA_TRY(cudaMemsetAsync(mixed, 0, sizeof(int), st));
         hydro_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(vel_e, rho, mass, perm, n, hp, vel_s,
-                                                           aux_s, mixed);
+                                                           aux_s);
         note_launch();
     }
     SPH_LAUNCH_CHECK();
@@ -398,7 +371,7 @@ int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, 
 
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp, int lanes, float4 *acc_out, const int *mixed, cudaStream_t st,
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st,
                   const float4 *grav, float C, float *dt_out, float *dt_min, float dt_cap) {
     const bool cfl = dt_min != nullptr;
     unsigned *bits = reinterpret_cast<unsigned *>(dt_min);
@@ -412,11 +385,11 @@ int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_
     if (cfl)                                                                                    \
         forces_kernel<G, true><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, \
                                                             nb_idx, cap, n, hp, acc_out, grav, C, \
-                                                            dt_out, bits, mixed);               \
+                                                            dt_out, bits);                      \
     else                                                                                        \
         forces_kernel<G, false><<<grid_for(T), 128, 0, st>>>(pos_h_s, vel_s, aux_s, perm, nb_start, \
                                                              nb_idx, cap, n, hp, acc_out, nullptr, \
-                                                             0.0f, nullptr, nullptr, mixed)
+                                                             0.0f, nullptr, nullptr)
         switch (lanes) {
             case 1: SPHGB_FORCES(1); break;
             case 2: SPHGB_FORCES(2); break;

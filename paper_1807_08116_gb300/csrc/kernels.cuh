@@ -110,8 +110,7 @@ int launch_density(const float4 *pos_h_s, const float *mass, const int *perm, co
                    const int *nb_idx, int cap, int n, float sigma, int lanes, float *rho_s,
                    float *rho_out, float *h_next_out, float *mass_s, int *mixed, cudaStream_t st);
 int launch_hydro_prep(const float4 *vel_e, const float *rho, const float *mass, const int *perm,
-                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, int *mixed,
-                      cudaStream_t st);
+                      int n, HydroParams hp, float4 *vel_s, float4 *aux_s, cudaStream_t st);
 // integrate.cu: integrate_step with the step size optionally read from
 // device memory (d_dt != NULL)
 int integrate_launch(int phase, double dt, const float *d_dt, int n, int n_gas, double *d_r,
@@ -127,7 +126,7 @@ int launch_cfl(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s, 
 // the same positions; *dt_min = min(dt_cap, smallest particle step))
 int launch_forces(const float4 *pos_h_s, const float4 *vel_s, const float4 *aux_s,
                   const int *perm, const int *nb_start, const int *nb_idx, int cap, int n,
-                  HydroParams hp, int lanes, float4 *acc_out, const int *mixed, cudaStream_t st,
+                  HydroParams hp, int lanes, float4 *acc_out, cudaStream_t st,
                   const float4 *grav = nullptr, float C = 0.0f, float *dt_out = nullptr,
                   float *dt_min = nullptr, float dt_cap = 0.0f);
 

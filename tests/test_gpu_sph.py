@@ -103,12 +103,13 @@ def test_forces_single_halo(orc, lanes):
     assert np.abs((m[:, None] * a[:, :3]).sum(0)).max() < 1e-5 * (m[:, None] * np.abs(a[:, :3])).sum()
 
 
-def test_equal_mass_loops_match_the_general_ones(orc):
-    # with all gas masses equal, density and forces read m_j (and P_j) from
-    # the row's own particle and vel_s, and aux_s only for approaching pairs;
-    # one particle's mass one ulp off sends both passes through the general
-    # loops.  Rows that do not have that particle as a neighbour must come out
-    # bitwise the same either way, and both runs match the oracle.
+def test_equal_mass_density_loop_matches_the_general_one(orc):
+    # with all gas masses equal, the density pass takes m_j from the row's own
+    # particle and reads no mass array; one particle's mass one ulp off sends
+    # it through the general loop.  Rows that do not have that particle as a
+    # neighbour must come out bitwise the same either way (density, h_next and
+    # the forces computed from the same densities), and both runs match the
+    # oracle.
     d = ics.single_halo(8192, 8192, seed=0)
     ph, mass, ve = _stirred(d)
     assert np.all(mass == mass[0])
