@@ -290,7 +290,9 @@ int sph_gravity_tune(int32_t R, int32_t S);
 
 /* The same g_i (and phi_i) as pp_gravity with every unordered pair evaluated
  * once (Newton's third law: one inverse cube serves both bodies, 16 instead
- * of 2 x 12 FP32 operations per pair).  Bodies are cut into blocks of 1024;
+ * of 2 x 12 FP32 operations per pair; 14 in a tile whose bodies all have the
+ * same mass, which leaves the mass out of the pair sums and applies it once
+ * per tile sum).  Bodies are cut into blocks of 1024;
  * each tile of block pairs (I <= J) is one CTA, and the per-tile partial
  * sums are accumulated exactly as 64-bit fixed-point integers whose scale is
  * set per launch from sum |m_j| and eps, so the result is bitwise

@@ -123,14 +123,14 @@ __device__ __forceinline__ void nb_accept(const NbArgs &a, int i, int j, bool co
 template <int MODE>
 __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
     constexpr bool FILL = MODE == NB_FILL || MODE == NB_FILL_LISTED;
-    // candidates of a batch as columns, so pairs of them feed packed FP32x2
-    // operations from 8-byte loads
-    __shared__ __align__(16) float s_cx[kNbWarps][32], s_cy[kNbWarps][32], s_cz[kNbWarps][32],
-        s_ch[kNbWarps][32];
+    // candidates of a batch in pairs, (x, x', y, y') and (z, z', h, h') per
+    // pair of slots, so a pair feeds packed FP32x2 operations from two
+    // 16-byte loads (33 slots with the padding one)
+    __shared__ __align__(16) float s_cq[kNbWarps][8 * 17];
     __shared__ int s_j[kNbWarps][32];
     __shared__ int s_stage[MODE == NB_STAGE ? kNbWarps : 1][MODE == NB_STAGE ? kStageSmem * kStageStride : 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *sqx = s_cx[wib], *sqy = s_cy[wib], *sqz = s_cz[wib], *sqh = s_ch[wib];
+    float *sq = s_cq[wib];
     int *sj = s_j[wib];
     int *sstage = s_stage[MODE == NB_STAGE ? wib : 0];
     const long long r = ((long long)blockIdx.x * kNbWarps + wib) * 32 + lane;
@@ -263,9 +263,31 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                             MZ = warp_maxf(in ? mhz : 0.0f), IH = warp_maxf(ihw);
                 const int NX = HX - LX + 1, NY = HY - LY + 1;
                 const int ncell = NX * NY * (HZ - LZ + 1);
+                // a probe lane's cell from its index by FP32 reciprocals: below
+                // 2^22 the estimate of each quotient is off by at most one, and
+                // one correction makes it exact (cheaper than integer division)
+                const float rNX = 1.0f / (float)NX, rNY = 1.0f / (float)NY;
+                const bool fdiv = ncell < (1 << 22);
                 for (int c0 = 0; c0 < ncell; c0 += 32) {
                     const int ct = c0 + lane;
-                    const int qx = ct / NX, ty = qx / NY;
+                    int qx, ty;
+                    if (fdiv) {
+                        qx = (int)__fmul_rn((float)ct, rNX);
+                        {
+                            const int rr = ct - qx * NX;
+                            if (rr < 0) --qx;
+                            else if (rr >= NX) ++qx;
+                        }
+                        ty = (int)__fmul_rn((float)qx, rNY);
+                        {
+                            const int rr = qx - ty * NY;
+                            if (rr < 0) --ty;
+                            else if (rr >= NY) ++ty;
+                        }
+                    } else {
+                        qx = ct / NX;
+                        ty = qx / NY;
+                    }
                     const int tx = LX + (ct - qx * NX), tyy = LY + (qx - ty * NY), tz = LZ + ty;
                     int s = 0, e = 0;
                     unsigned hm = 0u;
@@ -342,19 +364,21 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         if (ok) {
                             // coordinates negated: p + (-q) rounds as p - q
                             const int slot = __popc(okm & ((1u << lane) - 1u));
-                            sqx[slot] = -q.x;
-                            sqy[slot] = -q.y;
-                            sqz[slot] = -q.z;
-                            sqh[slot] = q.w;
+                            float *d = sq + 8 * (slot >> 1) + (slot & 1);
+                            d[0] = -q.x;
+                            d[2] = -q.y;
+                            d[4] = -q.z;
+                            d[6] = q.w;
                             sj[slot] = jl;
                         }
                         if ((nok & 1) && lane == 0) {
                             // an odd batch gets a padding column that fails
                             // every test (h = NaN)
-                            sqx[nok] = 0.0f;
-                            sqy[nok] = 0.0f;
-                            sqz[nok] = 0.0f;
-                            sqh[nok] = __uint_as_float(0x7fc00000u);
+                            float *d = sq + 8 * (nok >> 1) + 1;
+                            d[0] = 0.0f;
+                            d[2] = 0.0f;
+                            d[4] = 0.0f;
+                            d[6] = __uint_as_float(0x7fc00000u);
                         }
                         __syncwarp();
                         // the predicate over the batch first, two candidates
@@ -364,10 +388,10 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         // order, with no branch per candidate
                         unsigned acc = 0u;
                         for (int u = 0; u < nok; u += 2) {
-                            const float2 qx2 = *reinterpret_cast<const float2 *>(sqx + u);
-                            const float2 qy2 = *reinterpret_cast<const float2 *>(sqy + u);
-                            const float2 qz2 = *reinterpret_cast<const float2 *>(sqz + u);
-                            const float2 qh2 = *reinterpret_cast<const float2 *>(sqh + u);
+                            const float4 A = *reinterpret_cast<const float4 *>(sq + 4 * u);
+                            const float4 B = *reinterpret_cast<const float4 *>(sq + 4 * u + 4);
+                            const float2 qx2 = make_float2(A.x, A.y), qy2 = make_float2(A.z, A.w);
+                            const float2 qz2 = make_float2(B.x, B.y), qh2 = make_float2(B.z, B.w);
                             const float2 dx = __fadd2_rn(px2, qx2);
                             const float2 dy = __fadd2_rn(py2, qy2);
                             const float2 dz = __fadd2_rn(pz2, qz2);
