@@ -270,6 +270,33 @@ def test_batched_matches_oracle_per_simulation(orc, low_threshold, shape):
         assert prms <= RMS_TOL and pmx <= MAX_TOL, (s, prms, pmx)
 
 
+def test_batched_mixed_and_equal_masses(orc, low_threshold):
+    # one simulation of the batch with unequal masses (its full tiles take the
+    # general form) beside equal-mass ones (their full tiles take the
+    # equal-mass form): each against the oracle on its own
+    torch = need_gpu()
+    nv = low_threshold
+    from paper_1807_08116_gb300.sim import assemble_batch
+    lst = _batch_ics()
+    rng = np.random.default_rng(36)
+    lst[0] = dict(lst[0], m=lst[0]["m"] * rng.uniform(0.5, 1.5, len(lst[0]["m"])))
+    ic, go, do, so = assemble_batch(lst)
+    batch = nv.Batch(go, do, torch.as_tensor(so, device="cuda"))
+    pm = torch.as_tensor(pos_m_of(ic["r"], ic["m"]), device="cuda")
+    work = nv.pp_gravity_pairs_workspace(pm.shape[0])
+    out = torch.full_like(pm, float("nan"))
+    nv.pp_gravity_pairs_batched(batch, pm, out, work, flags=nv.SPH_GRAV_POTENTIAL)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    for s, d in enumerate(lst):
+        cols = np.concatenate([np.arange(go[s], go[s + 1]), ic["n_gas"] + np.arange(do[s], do[s + 1])])
+        acc, pot = orc.gravity(pos_m_of(d["r"], d["m"]))
+        rms, mx = err(got[cols, :3], acc)
+        assert rms <= RMS_TOL and mx <= MAX_TOL, (s, rms, mx)
+        prms, pmx = err(got[cols, 3:], pot[:, None])
+        assert prms <= RMS_TOL and pmx <= MAX_TOL, (s, prms, pmx)
+
+
 def test_batched_falls_back_without_scratch():
     torch = need_gpu()
     from paper_1807_08116_gb300 import native as nv
