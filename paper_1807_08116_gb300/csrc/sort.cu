@@ -546,26 +546,38 @@ __device__ __forceinline__ void block_max_to(unsigned v, unsigned *shared5, int 
     if (threadIdx.x == 0 && shared5[slot]) atomicMax(global, shared5[slot]);
 }
 
-// Particle i placed at sorted slot f (i < 0: this lane has none): its sorted
-// copies, and the bucket / super-cell / level statistics, aggregated over the
-// lanes that share a value (one atomic per run).  Called by all 32 lanes of a
-// warp together.
-__device__ __forceinline__ void place_sorted(const SortArgs &a, const GridDev &g, int i, int f,
+// A particle's data and its bin: level, cell and bucket.
+struct Binned {
+    float4 p;
+    int sim, k, l, cx, cy, cz;
+};
+
+__device__ __forceinline__ Binned bin_of(const SortArgs &a, const GridDev &g, int i) {
+    Binned b;
+    b.p = a.pos_h[i];
+    b.sim = a.sim_of ? a.sim_of[i] : 0;
+    b.k = bucket_of_particle(b.p, b.sim, g, b.l, b.cx, b.cy, b.cz);
+    return b;
+}
+
+// A binned particle placed at sorted slot f (have = false: this lane has
+// none): its sorted copies, and the bucket / super-cell / level statistics,
+// aggregated over the lanes that share a value (one atomic per run).  Called
+// by all 32 lanes of a warp together.
+__device__ __forceinline__ void place_binned(const SortArgs &a, int f, bool have, const Binned &b,
                                              int *s_cnt, unsigned *s_hmax) {
     const int lane = threadIdx.x & 31;
     int l = -1, k = -1;
     unsigned hb = 0u, sbit = 0xffffffffu;   // no super-cell bit reaches 2^31
-    if (i >= 0) {
-        const float4 p = a.pos_h[i];
-        a.pos_h_s[f] = p;
-        const int sim = a.sim_of ? a.sim_of[i] : 0;
-        if (a.sim_s) a.sim_s[f] = sim;
-        int cx, cy, cz;
-        k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
-        hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;
+    if (have) {
+        a.pos_h_s[f] = b.p;
+        if (a.sim_s) a.sim_s[f] = b.sim;
+        k = b.k;
+        l = b.l;
+        hb = (b.p.w > 0.0f) ? __float_as_uint(b.p.w) : 0u;
         if (a.occ)
-            sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
-                             l + kMaxLevels * sim, a.log2_B);
+            sbit = super_bit(b.cx >> kSuperShift, b.cy >> kSuperShift, b.cz >> kSuperShift,
+                             b.l + kMaxLevels * b.sim, a.log2_B);
     }
     {
         const unsigned peers = __match_any_sync(0xffffffffu, k);
@@ -582,6 +594,14 @@ __device__ __forceinline__ void place_sorted(const SortArgs &a, const GridDev &g
         atomicAdd(&s_cnt[l], __popc(peers));
         atomicMax(&s_hmax[l], hpeer);
     }
+}
+
+// Particle i (i < 0: none) placed at sorted slot f.
+__device__ __forceinline__ void place_sorted(const SortArgs &a, const GridDev &g, int i, int f,
+                                             int *s_cnt, unsigned *s_hmax) {
+    Binned b{};
+    if (i >= 0) b = bin_of(a, g, i);
+    place_binned(a, f, i >= 0, b, s_cnt, s_hmax);
 }
 
 __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
@@ -691,16 +711,18 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
     // that landed there among its bucket's members (adjacent slots, so the
     // bucket reads are shared by a warp) and puts it, its sorted copy and its
     // statistics in its final slot; only the particle's own data is a random
-    // read.  Buckets of more than RANK_MAX members are queued for phase F.
-    // The trip count is warp-uniform so that the warp-wide matches see
-    // every lane.
+    // read (its bucket is binned again from it rather than read from key).
+    // Buckets of more than RANK_MAX members are queued for phase F.  The trip
+    // count is warp-uniform so that the warp-wide matches see every lane.
     const int lane = tid & 31;
     for (long long w0 = gtid - lane; w0 < n; w0 += gstride) {
         const long long j = w0 + lane;
         int i = -1, k = -1, s = 0, e = 0;
+        Binned bn{};
         if (j < n) {
             i = a.tmp[j];
-            k = a.key[i];
+            bn = bin_of(a, g, i);
+            k = bn.k;
             s = a.start[k];
             e = a.start[k + 1];
             if (e - s > RANK_MAX) {
@@ -715,7 +737,7 @@ __global__ void __launch_bounds__(FS_THREADS) sort_fused_kernel(SortArgs a) {
             f = s + r;
             a.perm[f] = i;
         }
-        place_sorted(a, g, i, f, s_cnt, s_hmax);
+        place_binned(a, f, i >= 0, bn, s_cnt, s_hmax);
     }
     grid.sync();
 
