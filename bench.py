@@ -49,8 +49,8 @@ WORKLOAD_NAMES = {
 GFC_TRAFFIC = {
     "pp_gravity_kernel": {"file": "gravity.cu", "n": 4194304, "bytes": 870.39e6,
                           "sha256": "84874065d5e239daf0a7be2711544d692b425dceaf2c41660785f2920f804721"},
-    "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 2.348488192e9,
-                                "sha256": "adfee2b1486ee5c1b9a041279e86eeaf1739eb959e066b952894b93cbc54d85f"},
+    "pp_gravity_pairs_kernel": {"file": "gravity_pairs.cu", "n": 4194304, "bytes": 2.352522496e9,
+                                "sha256": "7525917b0ee5448cdc0289209f2f206f9d20dd0cbbfbb30a4ca339e567265a02"},
 }
 FLOP_PER_INTERACTION = 20   # the usual direct-N-body convention
 FP32_LANES_PER_SM = 128      # FP32 lanes per SM on Blackwell (4 partitions x 32)

@@ -381,8 +381,10 @@ pp_gravity_pairs_kernel(const float4 *__restrict__ pos, int n, int nb, int lg,
     const float sa1 = sc.s_acc1, sa2 = sc.s_acc2, sp1 = sc.s_pot1, sp2 = sc.s_pot2;
     // A tile whose bodies all have the same mass m0 (and no padding) takes
     // the sums without the mass factors, and m0 once per sum at the end.
+    // Without the mass a sum is bounded by B x 0.385 / eps^2, so eps must
+    // keep that far inside FP32 (any eps above 1e-15 does).
     const float m0 = pos[global_of(I * B)].w;
-    bool same = cnt == B && (I + 1) * B <= ns;
+    bool same = cnt == B && (I + 1) * B <= ns && eps2 > 1e-30f;
     for (int q = tid; q < B; q += THREADS) same = same && dB[q].z == m0;
 #pragma unroll
     for (int p = 0; p < RP; ++p) same = same && mi[p].x == m0 && mi[p].y == m0;
