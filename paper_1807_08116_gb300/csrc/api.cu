@@ -82,6 +82,7 @@ struct sph_ctx {
     float *rho_s, *mass_s;
     int *own, *rev, *row_len, *nb_start, *nb_idx;
     int *sim_s;      // simulation of each sorted particle (batched runs)
+    unsigned *tag_s; // cell tag of each sorted particle (level, low cell bits)
     int n_sorted;    // n_gas of the last sort
     int nb_built;    // 1 once lists match the last sort
     int sorted_batched;        // the last sort used the batch's simulation map
@@ -162,6 +163,7 @@ void carve(sph_ctx *c, char *base, size_t *total) {
     c->nb_start = cv.take<int>(n + 1);
     c->nb_idx = cv.take<int>((size_t)c->capacity);
     c->sim_s = cv.take<int>(n);
+    c->tag_s = cv.take<unsigned>(n);
     *total = (cv.off + 255) & ~size_t(255);
 }
 
@@ -343,6 +345,7 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
         fa.long_count = ctx->long_count;
         fa.pos_h_s = ctx->pos_h_s;
         fa.sim_s = sim_of ? ctx->sim_s : nullptr;
+        fa.tag_s = ctx->tag_s;
         fa.occ = ctx->occ;
         fa.log2_B = ctx->log2_M + 1;
         fa.hmax_cell = ctx->hmax_cell;
@@ -372,7 +375,7 @@ extern "C" int sph_bin_and_sort(sph_ctx *ctx, const float *d_pos_h, int32_t n_ga
             return rc;
         // sorted copies and the bucket / super-cell / level statistics
         if ((rc = launch_gather_bin(pos, sim_of, ctx->perm, n_gas, ctx->grid, ctx->pos_h_s,
-                                    sim_of ? ctx->sim_s : nullptr, ctx->occ, ctx->log2_M + 1,
+                                    sim_of ? ctx->sim_s : nullptr, ctx->tag_s, ctx->occ, ctx->log2_M + 1,
                                     ctx->hmax_cell, ctx->lvl_count, ctx->lvl_hmax, st)))
             return rc;
     }
@@ -409,6 +412,7 @@ extern "C" int sph_build_neighbors(sph_ctx *ctx, int32_t n_gas, int32_t *d_nb_st
     a.lvl_hmax = ctx->lvl_hmax;
     a.grid = ctx->grid;
     a.sim_s = ctx->sorted_batched ? ctx->sim_s : nullptr;
+    a.tag_s = ctx->tag_s;
     a.occ = ctx->occ;
     a.log2_B = ctx->log2_M + 1;
     a.n = n;

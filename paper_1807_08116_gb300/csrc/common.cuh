@@ -88,6 +88,14 @@ __device__ __forceinline__ unsigned super_bit(int sx, int sy, int sz, int l, int
     return (m + (unsigned)(l + 1) * (unsigned)kSuperSalt) & mask;
 }
 
+// Tag of (level, cell): the level and the low 9 bits of each cell
+// coordinate.  Two cells of one level share a tag only when they lie a
+// multiple of 512 cells apart on every axis where they differ.
+__device__ __forceinline__ unsigned cell_tag(int l, int cx, int cy, int cz) {
+    return ((unsigned)l << 27) | (((unsigned)cx & 511u) << 18) | (((unsigned)cy & 511u) << 9) |
+           ((unsigned)cz & 511u);
+}
+
 // FP32 neighbour predicate: ((dx*dx + dy*dy) + dz*dz) < (h_i + h_j)^2,
 // every operation rounded separately.
 __device__ __forceinline__ bool nb_pred(float4 a, float4 b) {

@@ -23,8 +23,9 @@ int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *gri
 // sorted copies (pos_h_s, and sim_s when sim_of is given) and the bucket,
 // super-cell and level statistics, taken over the sorted order
 int launch_gather_bin(const float4 *pos_h, const int *sim_of, const int *perm, int n,
-                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *occ, int log2_B,
-                      unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st);
+                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *tag_s, unsigned *occ,
+                      int log2_B, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
+                      cudaStream_t st);
 int launch_scatter(const int *key, int n, const int *start, int *count, int *perm, cudaStream_t st);
 // the whole sorting stage (grid, bin, scan, scatter, rank, long buckets,
 // sorted copies and statistics) as one cooperative launch; bitwise the
@@ -43,6 +44,7 @@ struct SortArgs {
     int block_sums_cap;     // entries of block_sums (bounds the grid)
     float4 *pos_h_s;
     int *sim_s;             // or NULL
+    unsigned *tag_s;        // cell tag of each sorted particle, or NULL
     unsigned *occ;
     int log2_B;
     unsigned *hmax_cell;
@@ -84,6 +86,7 @@ struct NbArgs {
     const unsigned *lvl_hmax;
     const GridDev *grid;
     const int *sim_s;        // [n] simulation of each sorted particle, or NULL (one simulation)
+    const unsigned *tag_s;   // [n] cell tag of each sorted particle (cell_tag), or NULL
     const unsigned *occ;     // super-cell occupancy bits, or NULL
     int log2_B;
     int n;

@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                 // one correction makes it exact (cheaper than integer division)
                 const float rNX = 1.0f / (float)NX, rNY = 1.0f / (float)NY;
                 const bool fdiv = ncell < (1 << 22);
+                // candidates identified by the sort's cell tags (a box under
+                // 512 cells on every axis), else by their level and cell
+                const bool tagged = a.tag_s && NX < 512 && NY < 512 && HZ - LZ < 511;
                 for (int c0 = 0; c0 < ncell; c0 += 32) {
                     const int ct = c0 + lane;
                     int qx, ty;
@@ -300,6 +303,7 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         hm = a.hmax_cell[k];
                     }
                     const unsigned live = __ballot_sync(kFull, s < e);
+                    const unsigned ptag = cell_tag(l, tx, tyy, tz);
                     if (live == 0u) continue;
                     const float ftx = (float)tx, fty = (float)tyy, ftz = (float)tz;
                     // the bucket's max h in cell units, by the lane that read it
@@ -345,18 +349,31 @@ __global__ void __launch_bounds__(kNbWarps * 32, 8) nb_kernel(NbArgs a) {
                         t = min(t, 31);
                         const int jl = __shfl_sync(kFull, s, t) + gi -
                                        (__shfl_sync(kFull, incl, t) - __shfl_sync(kFull, len, t));
-                        const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
-                                  cz = __shfl_sync(kFull, tz, t);
                         bool ok = gi < total && (unsigned)jl < (unsigned)a.n;
                         float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        if (ok) {
-                            // the identity checks (same simulation, level and
-                            // cell as the probed one), once per candidate
-                            q = a.pos_h_s[jl];
-                            ok = (!a.sim_s || a.sim_s[jl] == sg) &&
-                                 level_of(q.w, g.log2_L0, g.n_levels) == l &&
-                                 cell_of(q.x, g.x0, inv_c) == cx && cell_of(q.y, g.y0, inv_c) == cy &&
-                                 cell_of(q.z, g.z0, inv_c) == cz;
+                        // the identity checks (same simulation, level and cell
+                        // as the probed one), once per candidate
+                        if (tagged) {
+                            // the sort's cell tag: equal tags on one level mean
+                            // the same cell or one 512 cells away on some axis,
+                            // which lies outside a box under 512 cells wide and
+                            // so beyond every member's reach: the predicate
+                            // rejects it, and no candidate is taken twice
+                            const unsigned pt = __shfl_sync(kFull, ptag, t);
+                            if (ok) {
+                                q = a.pos_h_s[jl];
+                                ok = (!a.sim_s || a.sim_s[jl] == sg) && a.tag_s[jl] == pt;
+                            }
+                        } else {
+                            const int cx = __shfl_sync(kFull, tx, t), cy = __shfl_sync(kFull, tyy, t),
+                                      cz = __shfl_sync(kFull, tz, t);
+                            if (ok) {
+                                q = a.pos_h_s[jl];
+                                ok = (!a.sim_s || a.sim_s[jl] == sg) &&
+                                     level_of(q.w, g.log2_L0, g.n_levels) == l &&
+                                     cell_of(q.x, g.x0, inv_c) == cx && cell_of(q.y, g.y0, inv_c) == cy &&
+                                     cell_of(q.z, g.z0, inv_c) == cz;
+                            }
                         }
                         const unsigned okm = __ballot_sync(kFull, ok);
                         const int nok = __popc(okm);

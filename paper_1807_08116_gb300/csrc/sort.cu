@@ -152,7 +152,8 @@ __global__ void bin_kernel(const float4 *__restrict__ pos_h, const int *__restri
 __global__ void gather_bin_kernel(const float4 *__restrict__ pos_h, const int *__restrict__ sim_of,
                                   const int *__restrict__ perm, int n,
                                   const GridDev *__restrict__ gridp, float4 *__restrict__ pos_h_s,
-                                  int *__restrict__ sim_s, unsigned *__restrict__ occ, int log2_B,
+                                  int *__restrict__ sim_s, unsigned *__restrict__ tag_s,
+                                  unsigned *__restrict__ occ, int log2_B,
                                   unsigned *__restrict__ hmax_cell, int *__restrict__ lvl_count,
                                   unsigned *__restrict__ lvl_hmax) {
     __shared__ int s_cnt[kMaxLevels];
@@ -175,6 +176,7 @@ __global__ void gather_bin_kernel(const float4 *__restrict__ pos_h, const int *_
         if (sim_s) sim_s[j] = sim;
         int cx, cy, cz;
         k = bucket_of_particle(p, sim, g, l, cx, cy, cz);
+        if (tag_s) tag_s[j] = cell_tag(l, cx, cy, cz);
         hb = (p.w > 0.0f) ? __float_as_uint(p.w) : 0u;   // NaN / <= 0 -> 0
         if (occ)
             sbit = super_bit(cx >> kSuperShift, cy >> kSuperShift, cz >> kSuperShift,
@@ -572,6 +574,7 @@ __device__ __forceinline__ void place_binned(const SortArgs &a, int f, bool have
     if (have) {
         a.pos_h_s[f] = b.p;
         if (a.sim_s) a.sim_s[f] = b.sim;
+        if (a.tag_s) a.tag_s[f] = cell_tag(b.l, b.cx, b.cy, b.cz);
         k = b.k;
         l = b.l;
         hb = (b.p.w > 0.0f) ? __float_as_uint(b.p.w) : 0u;
@@ -861,11 +864,12 @@ int launch_bin(const float4 *pos_h, const int *sim_of, int n, const GridDev *gri
 }
 
 int launch_gather_bin(const float4 *pos_h, const int *sim_of, const int *perm, int n,
-                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *occ, int log2_B,
-                      unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax, cudaStream_t st) {
+                      const GridDev *grid, float4 *pos_h_s, int *sim_s, unsigned *tag_s, unsigned *occ,
+                      int log2_B, unsigned *hmax_cell, int *lvl_count, unsigned *lvl_hmax,
+                      cudaStream_t st) {
     if (n > 0) {
         gather_bin_kernel<<<blocks_for(n, 256), 256, 0, st>>>(pos_h, sim_of, perm, n, grid, pos_h_s,
-                                                              sim_s, occ, log2_B, hmax_cell,
+                                                              sim_s, tag_s, occ, log2_B, hmax_cell,
                                                               lvl_count, lvl_hmax);
         note_launch();
     }
