@@ -83,6 +83,20 @@ def test_gravity_traffic_only_while_the_kernel_source_is_unchanged(monkeypatch):
     assert bench.gfc_traffic(rec["n"], "pp_gravity_pairs_kernel") is None
 
 
+def test_fp32_operations_follow_the_masses():
+    import bench
+    # the pair-once kernel issues 7 FP32-pipe operations per ordered
+    # interaction when every tile takes the equal-mass form, 8 otherwise; the
+    # one-sided kernel 12 either way
+    eq = np.full(1000, 1e-3, np.float32)
+    mixed = eq.copy()
+    mixed[17] = np.nextafter(mixed[17], np.float32(1.0))
+    assert bench.fp32_ops("pp_gravity_pairs_kernel", eq) == 7
+    assert bench.fp32_ops("pp_gravity_pairs_kernel", mixed) == 8
+    assert bench.fp32_ops("pp_gravity_kernel", eq) == 12
+    assert bench.fp32_ops("pp_gravity_kernel", mixed) == 12
+
+
 def test_pairs_crossover_choice():
     from paper_1807_08116_gb300.tune import pairs_crossover
     # (one-sided ms, pair-once ms) per size
